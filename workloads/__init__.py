@@ -1,0 +1,203 @@
+"""Seeded synthetic inputs for the HashGraph workloads.
+
+This module generates the key and query arrays that both the CUDA path and
+the CPU oracle consume.  It holds no hash-table arithmetic: only SplitMix64
+streams and the recipes below (the C source is ``hg_workloads.c``; build it
+with :func:`build`).
+
+Recipes (master seed ``MASTER_SEED``; stream ids in ``STREAM``):
+
+* ``plain_uniform`` -- N uniform 32-bit keys (high half of each SplitMix64
+  output), Q queries of which a Bernoulli(``hit``) share are copies of a
+  uniformly chosen build key and the rest fresh uniform values.  The paper's
+  random-key experiments (Sec. 5.3) draw keys at random; its table size
+  equals the key count (load factor C = 1, Sec. 5.3).
+* ``zipf_large`` -- N 32-bit keys whose ranks follow Zipf(s=1) over 1..M,
+  value = rank * 0x9E3779B1 mod 2^32; queries hit with probability ``hit``
+  on a rank drawn uniformly from 1..M, misses use ranks above M (values that
+  never occur among the keys).  This is the duplicate-key regime of the
+  paper's Sec. 5.3 "Duplicate Keys" experiment.
+* ``join_kv`` -- N (uint64 key, uint32 value) pairs, and a probe relation
+  whose ``hot_frac`` share of slots holds ``rep`` copies each of hot keys;
+  every distinct probe key is a build key with probability 1/2, else fresh;
+  slots are Fisher-Yates shuffled.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "hg_workloads.c")
+LIB = os.path.join(HERE, "libhg_workloads.so")
+
+MASTER_SEED = 0x210400792
+STREAM = {
+    "keys": 1,
+    "values": 2,
+    "q_select": 3,
+    "q_miss": 4,
+    "shuffle": 5,
+}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the generator library with gcc (plain C, no arch-specific flags)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + ".tmp"
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+            "-o", tmp, SRC,
+        ])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB)
+        u64, vp = ctypes.c_uint64, ctypes.c_void_p
+        L.hgw_splitmix64_at.restype = u64
+        L.hgw_splitmix64_at.argtypes = [u64, u64]
+        L.hgw_stream.restype = u64
+        L.hgw_stream.argtypes = [u64, u64]
+        L.hgw_set_threads.argtypes = [ctypes.c_int]
+        L.hgw_uniform_u32.argtypes = [u64, u64, vp]
+        L.hgw_uniform_u64.argtypes = [u64, u64, vp]
+        L.hgw_probe_mix_u32.argtypes = [vp, u64, u64, u64, u64, u64, vp]
+        L.hgw_probe_mix_u64.argtypes = [vp, u64, u64, u64, u64, u64, vp]
+        L.hgw_zipf_table.argtypes = [u64, vp, vp]
+        L.hgw_zipf_guide_size.restype = u64
+        L.hgw_zipf_values_u32.argtypes = [vp, vp, u64, u64, u64, vp]
+        L.hgw_zipf_rank_of.restype = u64
+        L.hgw_zipf_rank_of.argtypes = [vp, vp, u64, u64]
+        L.hgw_rank_value.restype = ctypes.c_uint32
+        L.hgw_rank_value.argtypes = [u64]
+        L.hgw_zipf_queries_u32.argtypes = [u64, u64, u64, u64, u64, vp]
+        L.hgw_join_probe_u64.argtypes = [vp, u64, u64, u64, u64, u64, u64, u64, vp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def stream(name: str, master: int = MASTER_SEED, salt: int = 0) -> int:
+    """Stream state for a named purpose; ``salt`` separates per-table streams."""
+    return _load().hgw_stream(master, STREAM[name] + (salt << 8))
+
+
+def splitmix64_at(state: int, i: int) -> int:
+    return _load().hgw_splitmix64_at(state, i)
+
+
+def hit_threshold(p: float) -> int:
+    """Integer threshold on the high 32 bits of a draw: hit iff (x >> 32) < thr."""
+    return int(round(p * 2**32))
+
+
+def uniform_u32(state: int, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint32)
+    _load().hgw_uniform_u32(state, n, _ptr(out))
+    return out
+
+
+def uniform_u64(state: int, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint64)
+    _load().hgw_uniform_u64(state, n, _ptr(out))
+    return out
+
+
+def probe_mix(keys: np.ndarray, q: int, hit: float, sel: int, miss: int) -> np.ndarray:
+    keys = np.ascontiguousarray(keys)
+    out = np.empty(q, dtype=keys.dtype)
+    f = _load().hgw_probe_mix_u32 if keys.dtype == np.uint32 else _load().hgw_probe_mix_u64
+    f(_ptr(keys), keys.size, sel, miss, hit_threshold(hit), q, _ptr(out))
+    return out
+
+
+class ZipfTable:
+    """Partial harmonic sums S[0..M] and the guide table of the Zipf sampler."""
+
+    def __init__(self, M: int):
+        self.M = M
+        self.S = np.empty(M + 1, dtype=np.float64)
+        self.G = np.empty(_load().hgw_zipf_guide_size(), dtype=np.uint32)
+        _load().hgw_zipf_table(M, _ptr(self.S), _ptr(self.G))
+
+    def rank_of(self, x: int) -> int:
+        return _load().hgw_zipf_rank_of(_ptr(self.S), _ptr(self.G), self.M, x)
+
+    def values(self, state: int, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint32)
+        _load().hgw_zipf_values_u32(_ptr(self.S), _ptr(self.G), self.M, state, n, _ptr(out))
+        return out
+
+
+def rank_value(r: int) -> int:
+    return _load().hgw_rank_value(r)
+
+
+@dataclass
+class Workload:
+    """Inputs of one build + probe job."""
+    name: str
+    keys: np.ndarray
+    values: np.ndarray | None
+    queries: np.ndarray
+    num_buckets: int
+    seed: int = 0
+
+    @property
+    def key_bytes(self) -> int:
+        return self.keys.dtype.itemsize
+
+
+def plain_uniform(n: int = 1 << 20, q: int = 1 << 20, num_buckets: int | None = None,
+                  hit: float = 0.5, master: int = MASTER_SEED, salt: int = 0) -> Workload:
+    keys = uniform_u32(stream("keys", master, salt), n)
+    queries = probe_mix(keys, q, hit, stream("q_select", master, salt), stream("q_miss", master, salt))
+    return Workload("plain_uniform", keys, None, queries, num_buckets if num_buckets else max(n, 1))
+
+
+def zipf_queries(M: int, q: int, hit: float, master: int = MASTER_SEED, salt: int = 0) -> np.ndarray:
+    out = np.empty(q, dtype=np.uint32)
+    _load().hgw_zipf_queries_u32(M, stream("q_select", master, salt), stream("q_miss", master, salt),
+                                 hit_threshold(hit), q, _ptr(out))
+    return out
+
+
+_ZIPF_CACHE: dict[int, ZipfTable] = {}
+
+
+def zipf_table(M: int) -> ZipfTable:
+    if M not in _ZIPF_CACHE:
+        _ZIPF_CACHE[M] = ZipfTable(M)
+    return _ZIPF_CACHE[M]
+
+
+def zipf_large(n: int = 1 << 28, num_buckets: int = 1 << 27, q: int = 1 << 28, M: int = 1 << 24,
+               hit: float = 0.7, master: int = MASTER_SEED, salt: int = 0) -> Workload:
+    keys = zipf_table(M).values(stream("keys", master, salt), n)
+    queries = zipf_queries(M, q, hit, master, salt)
+    return Workload("zipf_large", keys, None, queries, num_buckets)
+
+
+def join_kv(n: int = 1 << 27, num_buckets: int = 1 << 26, q: int = 1 << 26, hot_frac: float = 0.05,
+            rep: int = 8, master: int = MASTER_SEED, salt: int = 0) -> Workload:
+    keys = uniform_u64(stream("keys", master, salt), n)
+    values = (uniform_u64(stream("values", master, salt), n) >> np.uint64(32)).astype(np.uint32)
+    hot = int(hot_frac * q) // rep
+    probe = np.empty(q, dtype=np.uint64)
+    _load().hgw_join_probe_u64(_ptr(keys), n, stream("q_select", master, salt), stream("q_miss", master, salt),
+                               stream("shuffle", master, salt), q, hot, rep, _ptr(probe))
+    return Workload("join_kv", keys, values, probe, num_buckets)
