@@ -1,0 +1,366 @@
+"""Benchmark: HashGraph build + probe throughput on one GB300 (or N replicas).
+
+One step = hg_build (hash, histogram, scan, scatter) + hg_query_count (counts
+and total) + hg_free over the large duplicate-key workload: 2^28 uint32 keys
+drawn Zipf(s=1) over 2^24 distinct values, 2^27 buckets, murmur3-fmix32 seed
+0, 2^28 queries with 70% hits.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Inputs (2 GiB per step) exceed the 129 MB L2, so no L2 flush is needed
+between steps.  Multi-GPU runs (torchrun) are independent replicas: every
+rank builds and probes its own table (weak scaling; no collective on the data
+path).  `--impl reference` times the CPU oracle (the only reference this
+method has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "build+probe Gkeys/s at 2^28 u32"
+UNIT = "Gkeys/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--log2n", type=int, default=28, help="log2 of build keys (queries equal, buckets half)")
+    p.add_argument("--cpu-sample-log2", type=int, default=24)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload_desc(log2n):
+    return (f"zipf_large: N=2^{log2n} uint32 keys Zipf(s=1) over 2^24 values, B=2^{log2n - 1} buckets, "
+            f"murmur3-fmix32 seed 0, Q=2^{log2n} queries 70% hits (ranks uniform over the 2^24 values)")
+
+
+def make_workload(log2n, salt):
+    import workloads as W
+    return W.zipf_large(n=1 << log2n, num_buckets=1 << (log2n - 1), q=1 << log2n, M=1 << 24, hit=0.7, salt=salt)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2104_00792_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_zipf_large.txt")
+    try:
+        rows = {}
+        with open(path) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    rows[k.strip()] = v.strip()
+    except OSError:
+        return None
+    if rows.get("source_hash") != source_hash():
+        return None
+    v = rows.get(f"traffic_bytes_per_launch.{kernel}")
+    return float(v) if v else None
+
+
+def cpu_oracle_sample(wl, log2s):
+    """Oracle build + count on the first 2^log2s keys and queries of the
+    workload, table size scaled to keep the same keys-per-bucket ratio."""
+    import numpy as np
+
+    import oracle
+    n = min(1 << log2s, wl.keys.size)
+    keys = np.ascontiguousarray(wl.keys[:n])
+    queries = np.ascontiguousarray(wl.queries[:n])
+    B = max(1, (wl.num_buckets * n) // wl.keys.size)
+    t0 = time.perf_counter()
+    t = oracle.build_table(keys, B, 0)
+    t.query_count(queries)
+    dt = time.perf_counter() - t0
+    return {"value": (2 * n) / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first 2^{log2s} keys and 2^{log2s} queries of the workload, B={B} (same keys/bucket), "
+                      f"build+count, {dt:.2f} s single-threaded"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = make_workload(args.log2n, 0)
+    times = []
+    res = None
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, args.cpu_sample_log2 - 2)
+    for _ in range(args.steps):
+        res = cpu_oracle_sample(wl, args.cpu_sample_log2 - 2)
+        times.append(res["value"])
+    v = statistics.median(times)
+    res["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload_desc(args.log2n), "reference": "CPU oracle (oracle/hg_oracle.c)"},
+            "cpu_baseline": res, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2104_00792_gb300 as hg
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    wl = make_workload(args.log2n, rank)
+    N, Q, B = wl.keys.size, wl.queries.size, wl.num_buckets
+    keys = torch.from_numpy(wl.keys.view(np.int32)).to(dev)
+    queries = torch.from_numpy(wl.queries.view(np.int32)).to(dev)
+    counts = torch.empty(Q, dtype=torch.int32, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        t = hg.hg_build(keys, B, 0, stream=stream)
+        hg.hg_query_count(t, queries, counts, total, stream=stream)
+        t.free(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # byte model inputs (outside the timed region)
+    with hg.hg_build(keys, B, 0, stream=stream) as t:
+        walk = hg.hg_probe_stats(t, queries, stream=stream)
+    torch.cuda.synchronize(dev)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0)
+    with sampler:
+        time.sleep(0.3)
+        barrier()
+        torch.cuda.synchronize(dev)
+        hg.hg_prof_enable(True)
+        launches0 = hg.hg_launch_count()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        launches = hg.hg_launch_count() - launches0
+        hg.hg_prof_enable(False)
+        barrier()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        prof = {name: hg.hg_prof_read(name) for name in hg.hg_prof_names()}
+
+        # end to end through the C ABI with host buffers: pinned inputs copied in,
+        # counts and total copied out, inside the timed region
+        e2e = None
+        if not args.no_e2e:
+            h_keys = torch.from_numpy(wl.keys.view(np.int32)).pin_memory()
+            h_q = torch.from_numpy(wl.queries.view(np.int32)).pin_memory()
+            h_counts = torch.empty(Q, dtype=torch.int32).pin_memory()
+            h_total = torch.empty(1, dtype=torch.int64).pin_memory()
+
+            def e2e_step():
+                keys.copy_(h_keys, non_blocking=True)
+                queries.copy_(h_q, non_blocking=True)
+                step()
+                h_counts.copy_(counts, non_blocking=True)
+                h_total.copy_(total, non_blocking=True)
+
+            for _ in range(2):
+                e2e_step()
+            torch.cuda.synchronize(dev)
+            barrier()
+            e_steps = max(3, args.steps // 3)
+            ev0.record(stream)
+            for _ in range(e_steps):
+                e2e_step()
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            barrier()
+            e2e_ms = ev0.elapsed_time(ev1) / e_steps
+            e2e = {"ms": e2e_ms, "h2d": 4 * (N + Q), "d2h": 4 * Q + 8}
+        time.sleep(0.2)
+
+    # max over ranks
+    if dist is not None:
+        tt = torch.tensor([ms, e2e["ms"] if e2e else 0.0], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt[0])
+        if e2e:
+            e2e["ms"] = float(tt[1])
+
+    # sanity: the total equals the sum of counts of the last step
+    ok_total = int(total.cpu().numpy().view(np.uint64)[0]) == int(counts.cpu().numpy().view(np.uint32).sum(dtype=np.uint64))
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    value = world * (N + Q) / (ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    # algorithmic bytes per launch of each kernel (k = 4 key bytes, v = 0, o = 4 offset bytes)
+    k, o = 4, 4
+    W, WL = walk["walked"], walk["walked_long"]
+    model = {
+        "hist": k * N + 4 * B,
+        "scan": 4 * (B + 1) + o * (B + 1),
+        "scatter": 2 * k * N + o * B,
+        "probe": k * Q + 8 * Q + k * (W - WL) + 4 * Q,
+        "long": k * WL,
+    }
+    per_kernel = {}
+    for name, (n_launch, tot_ms) in prof.items():
+        if n_launch:
+            per_kernel[name] = {"launches": n_launch, "ms_per_launch": tot_ms / n_launch,
+                                "share": None, "model_bytes": model.get(name)}
+    tot = sum(v["ms_per_launch"] * v["launches"] for v in per_kernel.values()) or 1.0
+    for v in per_kernel.values():
+        v["share"] = v["ms_per_launch"] * v["launches"] / tot
+    dom = max((n for n in per_kernel if n in model), key=lambda n: per_kernel[n]["share"])
+    d = per_kernel[dom]
+    achieved = model[dom] / (d["ms_per_launch"] * 1e-3) / 1e9
+    step_bytes = sum(model.values())
+    clocks = sampler.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_desc(args.log2n), "parallelism": f"replicas{world}",
+                   "l2": "inputs exceed L2 (2 GiB read per step); no flush",
+                   "step": "hg_build + hg_query_count(counts, total) + hg_free"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(dom), "peak_kind": peak_kind,
+                     "step_model_bytes": step_bytes,
+                     "step_frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
+        "kernels": per_kernel,
+        "walk": walk,
+        "gpu_launches": launches,
+        "clocks": {k2: clocks[k2] for k2 in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "check": {"total_equals_sum_of_counts": ok_total},
+    }
+    if e2e:
+        line["e2e"] = {"value": world * (N + Q) / (e2e["ms"] * 1e-3) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                       "ms_per_step": e2e["ms"]}
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(wl, args.cpu_sample_log2)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * hashgraph.h -- C ABI of libhashgraph.so, a single-GPU HashGraph static hash
+ * table for sm_103a.
+ *
+ * The table is the CSR ("bipartite graph") layout of HashGraph (Multi-GPU
+ * HashGraph paper, Sec. 3.1): an offset array over the V = num_buckets
+ * hashed values and a keys array of length N grouped by hashed value, so the
+ * keys that hash to bucket i are keys[offset[i]] .. keys[offset[i+1] - 1].
+ * Building it is Algorithm 1 (hash, count per bucket, prefix sum, scatter);
+ * a query hashes the probe key and walks its bucket (Sec. 3.3), counting
+ * every equal key (duplicates included, Sec. 5.5).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are CUDA device memory on the calling thread's
+ *    current device; h_* are host memory.  Key arrays hold uint32_t
+ *    (key_bytes = 4) or uint64_t (key_bytes = 8) elements, naturally aligned;
+ *    16-byte aligned arrays take the vectorised load path.
+ *  - Every call is ordered on the caller's stream `s` (a cudaStream_t; NULL
+ *    is the legacy default stream) and returns without waiting for the GPU,
+ *    except where stated.  Input buffers are borrowed: they must stay valid
+ *    and unmodified until the stream has passed the call.
+ *  - Argument errors are reported synchronously and leave no work queued.
+ *    Errors found by kernels (a bounded wait that ran out) are recorded in the
+ *    table's device error word and reported by hg_sync().
+ *  - No call throws across the ABI; hg_last_error() gives a message for the
+ *    calling thread's last non-HG_OK status.
+ *  - hash(k) = fmix32(k ^ (uint32_t)seed) for 32-bit keys and
+ *    fmix64(k ^ seed) for 64-bit keys (the MurmurHash3 finalisers; the paper
+ *    names Murmur, Sec. 4.2); bucket(k) = hash(k) mod num_buckets, the
+ *    unsigned remainder (Algorithm 1, first loop).
+ */
+#ifndef HASHGRAPH_H
+#define HASHGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so that the header needs no CUDA headers. */
+typedef struct CUstream_st* hg_stream_t;
+
+typedef struct hg_table hg_table; /* opaque; owns its device arrays */
+
+typedef enum {
+    HG_OK = 0,
+    HG_ERR_INVALID_ARG = 1, /* a NULL or out-of-range argument; nothing was queued */
+    HG_ERR_OOM = 2,         /* a device allocation failed */
+    HG_ERR_CUDA = 3,        /* a CUDA runtime call failed; see hg_last_error() */
+    HG_ERR_CAPACITY = 4,    /* hg_query_gather: out_capacity < number of matches */
+    HG_ERR_NO_VALUES = 5,   /* hg_query_gather on a table without values */
+    HG_ERR_TIMEOUT = 6      /* a kernel's bounded wait ran out (reported by hg_sync) */
+} hg_status;
+
+/* hg_config.flags */
+#define HG_INDEX_VALUES 0x1u  /* key-only input: store each key's input index as its value (Sec. 2: the
+                                 value "can be the index in the original input array") */
+#define HG_PLAIN_BUILD 0x2u   /* force the direct Algorithm 1 build (global atomics, no partition pass) */
+#define HG_PARTITION_BUILD 0x4u /* force the partitioned build (keys binned by bucket range first, the
+                                   "efficient HashGraph" of Sec. 3.2) */
+
+typedef struct {
+    uint32_t key_bytes;   /* 4 or 8 */
+    uint32_t value_bytes; /* 0 (keys only) or 4 (uint32_t values) */
+    uint64_t num_buckets; /* V in Algorithm 1; 1 <= V <= 2^31 (the paper's 32-bit table size, Sec. 4.3) */
+    uint64_t seed;        /* hash seed, XORed into the key before the finaliser */
+    uint32_t flags;       /* HG_* flags above */
+} hg_config;
+
+/* Message for the calling thread's most recent failing call ("" if none). Never NULL. */
+const char* hg_last_error(void);
+
+/* Library version string. */
+const char* hg_version(void);
+
+/*
+ * hg_build -- Algorithm 1: hash every key, count keys per bucket, exclusive
+ * prefix sum of the counts into offset[0..V] (offset[V] = n), scatter keys
+ * (and values) into their buckets' ranges.
+ *   cfg       table parameters (read during the call only)
+ *   d_keys    n keys of cfg->key_bytes each (may be NULL when n == 0)
+ *   d_values  n uint32_t values when cfg->value_bytes == 4, else NULL
+ *   n         number of keys, 0 <= n < 2^32 (offsets are 32-bit)
+ *   out       receives the new table; the table owns offsets (V+1 uint32_t),
+ *             keys (n) and values (n, if any), allocated stream-ordered on s
+ * The order of keys inside one bucket is unspecified.  Any key value is
+ * legal (no sentinel).  On error *out is NULL and nothing stays allocated.
+ */
+hg_status hg_build(const hg_config* cfg, const void* d_keys, const void* d_values, uint64_t n,
+                   hg_stream_t s, hg_table** out);
+
+/*
+ * hg_query_count -- for each query slot i, d_counts[i] = number of table keys
+ * equal to d_queries[i] (bucket walk, Sec. 3.3; duplicates counted, Sec. 5.5).
+ *   d_queries  q keys of the table's key width
+ *   d_counts   q uint32_t outputs (may be NULL if d_total is given)
+ *   d_total    optional single uint64_t: receives the sum of the counts (the
+ *              join cardinality); may be NULL
+ * Requires q < 2^32.
+ */
+hg_status hg_query_count(const hg_table* t, const void* d_queries, uint64_t q, uint32_t* d_counts,
+                         uint64_t* d_total, hg_stream_t s);
+
+/*
+ * hg_query_gather -- values of every matching key, grouped per query slot.
+ *   d_out_offsets  q+1 uint64_t: d_out_offsets[i] .. d_out_offsets[i+1] is slot
+ *                  i's segment of d_out_values; d_out_offsets[q] = total
+ *   d_out_values   out_capacity uint32_t slots (may be NULL if out_capacity == 0)
+ *   h_total        host pointer, receives the total number of matches
+ * Two-call pattern: this call synchronises `s` to read the total; if
+ * out_capacity < total it returns HG_ERR_CAPACITY with *h_total and
+ * d_out_offsets filled and d_out_values untouched.  Order inside a segment
+ * is unspecified.  A table built without values and without HG_INDEX_VALUES
+ * returns HG_ERR_NO_VALUES.
+ */
+hg_status hg_query_gather(const hg_table* t, const void* d_queries, uint64_t q, uint64_t* d_out_offsets,
+                          uint32_t* d_out_values, uint64_t out_capacity, uint64_t* h_total, hg_stream_t s);
+
+/*
+ * hg_join_count -- *d_total = sum over query slots of their counts, i.e. the
+ * inner-join cardinality of the table's keys with the queries.  d_total is one
+ * device uint64_t, overwritten (not accumulated).
+ */
+hg_status hg_join_count(const hg_table* t, const void* d_queries, uint64_t q, uint64_t* d_total,
+                        hg_stream_t s);
+
+/* Stream-ordered release of the table's arrays; the host struct is freed at once. NULL is OK. */
+hg_status hg_free(hg_table* t, hg_stream_t s);
+
+/*
+ * hg_sync -- wait for `s`, then read and clear the table's device error word.
+ * Returns HG_ERR_TIMEOUT if a kernel gave up a bounded wait since the last
+ * hg_sync, HG_ERR_CUDA on an asynchronous CUDA error or when a kernel found
+ * offsets inconsistent with the keys (the affected writes are skipped, never
+ * made out of bounds), else HG_OK.
+ */
+hg_status hg_sync(const hg_table* t, hg_stream_t s);
+
+/*
+ * hg_table_view -- borrow the table's device arrays (valid until hg_free):
+ * offsets (uint32_t[V+1]), keys (n elements), values (uint32_t[n] or NULL).
+ * Any output pointer may be NULL.
+ */
+hg_status hg_table_view(const hg_table* t, const void** d_offsets, const void** d_keys,
+                        const void** d_values, uint64_t* n, uint64_t* num_buckets);
+
+/*
+ * hg_probe_stats -- byte-model helper for diagnostics (not part of a query):
+ * for the query slots, d_stats[0] = W, the total number of keys their bucket
+ * walks visit (sum of offset[b+1] - offset[b] over slots); d_stats[1] = the
+ * part of W in buckets longer than the warp-walk limit (walked by the chunked
+ * long-bucket kernel); d_stats[2] = the number of such slots; d_stats[3] =
+ * that limit.  d_stats: 4 device uint64_t, overwritten.
+ */
+hg_status hg_probe_stats(const hg_table* t, const void* d_queries, uint64_t q, uint64_t* d_stats, hg_stream_t s);
+
+/* Number of kernels this process has launched through the library so far. */
+uint64_t hg_launch_count(void);
+
+/*
+ * Per-kernel timing for diagnostics.  While enabled, every kernel the library
+ * launches is bracketed by CUDA events on its launching stream.
+ * hg_prof_enable(1) also clears the records.  hg_prof_read() synchronises the
+ * recorded events and returns, for the kernel named `name` (e.g. "probe"),
+ * its launch count and total milliseconds; unknown names give 0 launches.
+ * hg_prof_names() returns a comma-separated list of the known kernel names.
+ */
+hg_status hg_prof_enable(int on);
+hg_status hg_prof_read(const char* name, uint64_t* launches, double* total_ms);
+const char* hg_prof_names(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HASHGRAPH_H */

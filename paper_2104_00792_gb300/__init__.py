@@ -1,0 +1,233 @@
+"""Python binding of libhashgraph.so (C ABI in include/hashgraph.h).
+
+Argument marshalling only: every step of the build and of the probes runs in
+the library's CUDA kernels.  PyTorch supplies device memory and streams.  The
+functions keep the C names (``hg_build``, ``hg_query_count``, ...); tensors
+must be contiguous CUDA tensors on the current device.
+
+There is no CPU fallback: importing this package fails if the compiled
+library is missing (build it with ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhashgraph.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: the CUDA library has not been built "
+        "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+HG_OK = 0
+HG_ERR_INVALID_ARG = 1
+HG_ERR_OOM = 2
+HG_ERR_CUDA = 3
+HG_ERR_CAPACITY = 4
+HG_ERR_NO_VALUES = 5
+HG_ERR_TIMEOUT = 6
+STATUS_NAMES = {0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_OOM", 3: "HG_ERR_CUDA",
+                4: "HG_ERR_CAPACITY", 5: "HG_ERR_NO_VALUES", 6: "HG_ERR_TIMEOUT"}
+
+HG_INDEX_VALUES = 0x1
+HG_PLAIN_BUILD = 0x2
+HG_PARTITION_BUILD = 0x4
+
+
+class hg_config(ctypes.Structure):
+    _fields_ = [("key_bytes", ctypes.c_uint32), ("value_bytes", ctypes.c_uint32),
+                ("num_buckets", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+
+
+_vp, _u64, _u32p = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p
+lib.hg_last_error.restype = ctypes.c_char_p
+lib.hg_version.restype = ctypes.c_char_p
+lib.hg_build.argtypes = [ctypes.POINTER(hg_config), _vp, _vp, _u64, _vp, ctypes.POINTER(_vp)]
+lib.hg_query_count.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp]
+lib.hg_query_gather.argtypes = [_vp, _vp, _u64, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]
+lib.hg_join_count.argtypes = [_vp, _vp, _u64, _vp, _vp]
+lib.hg_free.argtypes = [_vp, _vp]
+lib.hg_sync.argtypes = [_vp, _vp]
+lib.hg_table_view.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                              ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
+lib.hg_probe_stats.argtypes = [_vp, _vp, _u64, _vp, _vp]
+lib.hg_launch_count.restype = _u64
+lib.hg_prof_enable.argtypes = [ctypes.c_int]
+lib.hg_prof_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)]
+lib.hg_prof_names.restype = ctypes.c_char_p
+for _f in ("hg_build", "hg_query_count", "hg_query_gather", "hg_join_count", "hg_free", "hg_sync",
+           "hg_table_view", "hg_prof_enable", "hg_prof_read", "hg_probe_stats"):
+    getattr(lib, _f).restype = ctypes.c_int
+
+
+class HashGraphError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status: int) -> int:
+    if status != HG_OK:
+        raise HashGraphError(status, lib.hg_last_error().decode())
+    return status
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr() if t.numel() else None
+
+
+_KEY_DTYPES = {torch.int32: 4, torch.uint32: 4, torch.int64: 8, torch.uint64: 8}
+
+
+class Table:
+    """Handle of a device-resident HashGraph (owns the library's hg_table*)."""
+
+    def __init__(self, handle: int, key_bytes: int, n: int, num_buckets: int, has_values: bool, stream: int):
+        self.handle = handle
+        self.key_bytes = key_bytes
+        self.n = n
+        self.num_buckets = num_buckets
+        self.has_values = has_values
+        self._stream = stream
+
+    def free(self, stream=None):
+        if self.handle:
+            _check(lib.hg_free(self.handle, _stream(stream) if stream is not None else self._stream))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hg_build(keys: torch.Tensor, num_buckets: int, seed: int = 0, values: torch.Tensor | None = None,
+             flags: int = 0, stream=None) -> Table:
+    """hg_build: Algorithm 1 on the device.  keys: 32- or 64-bit integer tensor."""
+    if keys.dtype not in _KEY_DTYPES:
+        raise TypeError(f"keys dtype {keys.dtype} is not a 32/64-bit integer type")
+    kb = _KEY_DTYPES[keys.dtype]
+    if values is not None and values.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("values must be 32-bit")
+    cfg = hg_config(kb, 4 if values is not None else 0, num_buckets, seed & ((1 << 64) - 1), flags)
+    out = _vp()
+    s = _stream(stream)
+    _check(lib.hg_build(ctypes.byref(cfg), _ptr(keys), _ptr(values), keys.numel(), s, ctypes.byref(out)))
+    return Table(out.value, kb, keys.numel(), num_buckets, values is not None or bool(flags & HG_INDEX_VALUES), s)
+
+
+def hg_query_count(table: Table, queries: torch.Tensor, counts: torch.Tensor | None = None,
+                   total: torch.Tensor | None = None, stream=None):
+    """hg_query_count: per-slot multiplicities into `counts` (uint32/int32) and/or their sum into `total`."""
+    _check(lib.hg_query_count(table.handle, _ptr(queries), queries.numel(), _ptr(counts), _ptr(total),
+                              _stream(stream)))
+    return counts, total
+
+
+def hg_join_count(table: Table, queries: torch.Tensor, total: torch.Tensor, stream=None) -> torch.Tensor:
+    """hg_join_count: total[0] = sum of per-slot counts (inner-join cardinality)."""
+    _check(lib.hg_join_count(table.handle, _ptr(queries), queries.numel(), _ptr(total), _stream(stream)))
+    return total
+
+
+def hg_query_gather(table: Table, queries: torch.Tensor, out_offsets: torch.Tensor,
+                    out_values: torch.Tensor | None, stream=None) -> int:
+    """hg_query_gather: returns the total match count; raises HashGraphError(HG_ERR_CAPACITY)
+    when out_values is too small (out_offsets is filled in that case)."""
+    total = _u64(0)
+    cap = 0 if out_values is None else out_values.numel()
+    st = lib.hg_query_gather(table.handle, _ptr(queries), queries.numel(), _ptr(out_offsets),
+                             _ptr(out_values) if cap else None, cap, ctypes.byref(total), _stream(stream))
+    if st != HG_OK:
+        err = HashGraphError(st, lib.hg_last_error().decode())
+        err.total = total.value
+        raise err
+    return total.value
+
+
+def hg_free(table: Table, stream=None):
+    table.free(stream)
+
+
+def hg_sync(table: Table, stream=None):
+    _check(lib.hg_sync(table.handle, _stream(stream)))
+
+
+class _DeviceArray:
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"data": (ptr or 0, True), "shape": (n,), "typestr": typestr,
+                                         "version": 3, "strides": None}
+
+
+def hg_table_view(table: Table):
+    """(offsets, keys, values or None) as zero-copy CUDA tensors over the table's arrays.
+
+    The tensors use signed dtypes of the same width (int32 offsets and values,
+    int32/int64 keys); reinterpret them as unsigned on the host."""
+    o, k, v = _vp(), _vp(), _vp()
+    n, B = _u64(), _u64()
+    _check(lib.hg_table_view(table.handle, ctypes.byref(o), ctypes.byref(k), ctypes.byref(v), ctypes.byref(n),
+                             ctypes.byref(B)))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    offs = torch.as_tensor(_DeviceArray(o.value, B.value + 1, "<i4"), device=dev)
+    keys = torch.as_tensor(_DeviceArray(k.value, n.value, "<i4" if table.key_bytes == 4 else "<i8"), device=dev)
+    vals = None
+    if v.value:
+        vals = torch.as_tensor(_DeviceArray(v.value, n.value, "<i4"), device=dev)
+    return offs, keys, vals
+
+
+def hg_probe_stats(table: Table, queries: torch.Tensor, stream=None) -> dict:
+    """Walked-length statistics of the byte model (synchronises the stream)."""
+    st = torch.empty(4, dtype=torch.int64, device=queries.device)
+    _check(lib.hg_probe_stats(table.handle, _ptr(queries), queries.numel(), _ptr(st), _stream(stream)))
+    w, wl, nl, lim = (int(x) for x in st.cpu().tolist())
+    return {"walked": w, "walked_long": wl, "long_slots": nl, "warp_limit": lim}
+
+
+def hg_launch_count() -> int:
+    return lib.hg_launch_count()
+
+
+def hg_prof_enable(on: bool = True):
+    _check(lib.hg_prof_enable(1 if on else 0))
+
+
+def hg_prof_read(name: str):
+    n = _u64()
+    ms = ctypes.c_double()
+    _check(lib.hg_prof_read(name.encode(), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def hg_prof_names() -> list[str]:
+    return lib.hg_prof_names().decode().split(",")
+
+
+def hg_version() -> str:
+    return lib.hg_version().decode()

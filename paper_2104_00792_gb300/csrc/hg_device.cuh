@@ -1,0 +1,116 @@
+// Device-side helpers shared by the build and probe kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hg_internal.h"
+
+namespace hg {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// MurmurHash3 32-bit finaliser.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// MurmurHash3 64-bit finaliser.
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// bucket(k) = hash(k) mod B (Algorithm 1, first loop).  B <= 2^31, so a bucket fits 32 bits.
+__device__ __forceinline__ uint32_t bucket_of(uint32_t k, const Hasher& H) {
+    const uint32_t h = fmix32(k ^ (uint32_t)H.seed);
+    if (H.mode == MODE_POW2) return h & (uint32_t)H.mask;
+    return (uint32_t)__umul64hi(H.magic * (uint64_t)h, H.B);
+}
+__device__ __forceinline__ uint32_t bucket_of(uint64_t k, const Hasher& H) {
+    const uint64_t h = fmix64(k ^ H.seed);
+    if (H.mode == MODE_POW2) return (uint32_t)(h & H.mask);
+    return (uint32_t)(h % H.B);
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// Streaming 16-byte load that does not allocate in L1.
+__device__ __forceinline__ uint4 ld_stream16(const void* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+template <typename K>
+struct KeyVec {
+    static constexpr int N = 16 / sizeof(K);
+    K k[N];
+};
+
+template <typename K>
+__device__ __forceinline__ KeyVec<K> load_keys16(const K* p) {
+    uint4 raw = ld_stream16(p);
+    KeyVec<K> v;
+    static_assert(sizeof(v) == 16, "");
+    *reinterpret_cast<uint4*>(&v) = raw;
+    return v;
+}
+
+// Warp-aggregated atomic increment: every lane in `mask` adds 1 to ctr[b] and
+// gets back a distinct slot (old value + its rank among lanes with the same b).
+// Lanes with equal b share one atomic, so hot duplicate keys do not serialise.
+__device__ __forceinline__ uint32_t agg_inc(uint32_t* ctr, uint32_t b, unsigned mask) {
+    const unsigned peers = __match_any_sync(mask, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(ctr + b, (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & lanemask_lt());
+}
+
+// Same, when the old value is not needed (compiles to a reduction).
+__device__ __forceinline__ void agg_count(uint32_t* ctr, uint32_t b, unsigned mask) {
+    const unsigned peers = __match_any_sync(mask, b);
+    if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(ctr + b, (uint32_t)__popc(peers));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(FULL_MASK, v, o);
+        if ((int)lane_id() >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace hg

@@ -1,0 +1,85 @@
+// Internal host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hashgraph.h"
+
+namespace hg {
+
+// Device-side error bits (the table's error word).
+enum : uint32_t {
+    DEVERR_TIMEOUT = 1u,   // a decoupled-lookback wait ran out
+    DEVERR_BOUNDS = 2u,    // an index derived from the offsets fell outside its array (access skipped)
+};
+
+// bucket(k) = hash(k) mod B, with the remainder computed one of three ways
+// that all equal the unsigned '%' (checked by the tests):
+//   MODE_POW2    B = 2^j: hash & (B - 1)
+//   MODE_FAST32  32-bit hash, B < 2^32: Lemire, Kaser and Kurz, "Faster
+//                remainder by direct computation" (2019):
+//                M = floor((2^64 - 1) / B) + 1, r = mulhi64(M * h, B)
+//   MODE_DIV64   64-bit hash, B not a power of two: hardware-emulated '%'
+struct Hasher {
+    uint64_t seed;
+    uint64_t B;
+    uint64_t mask;
+    uint64_t magic;
+    uint32_t mode;
+};
+enum : uint32_t { MODE_POW2 = 0, MODE_FAST32 = 1, MODE_DIV64 = 2 };
+
+Hasher make_hasher(uint32_t key_bytes, uint64_t B, uint64_t seed);
+
+struct Table {
+    uint32_t key_bytes = 4;
+    uint32_t has_values = 0;  // values array present (user values or input indices)
+    uint32_t flags = 0;
+    int device = 0;
+    uint64_t n = 0;
+    uint64_t B = 0;
+    uint64_t seed = 0;
+    Hasher H{};
+    uint32_t* offsets = nullptr;  // B + 1
+    void* keys = nullptr;         // n
+    uint32_t* values = nullptr;   // n or null
+    uint32_t* err = nullptr;      // device error word
+};
+
+// Stream-ordered allocation from the device's default memory pool.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// Kernel launch bookkeeping (launch counter and optional per-kernel events).
+void launch_begin(const char* name, cudaStream_t s);
+void launch_end(const char* name, cudaStream_t s);
+int num_sms();
+
+// Build (Algorithm 1): fills t.offsets, t.keys, t.values.  Returns a CUDA error.
+cudaError_t build_table(Table& t, const void* d_keys, const void* d_values, cudaStream_t s);
+
+// Probe entry points.  Return a CUDA error.
+//   counts: u32 per slot (may be null); total: u64 sum (may be null).
+cudaError_t probe_count(const Table& t, const void* d_q, uint64_t q, uint32_t* counts, uint64_t* total,
+                        cudaStream_t s);
+// Gather, phase 1: per-slot counts into out_offsets and exclusive scan (out_offsets[q] = total).
+// Keeps the long-bucket work list in *ctx for phase 2.
+struct GatherCtx {
+    void* scratch = nullptr;
+    uint64_t slots = 0;
+};
+cudaError_t gather_offsets(const Table& t, const void* d_q, uint64_t q, uint64_t* out_offsets, GatherCtx* ctx,
+                           cudaStream_t s);
+cudaError_t gather_values(const Table& t, const void* d_q, uint64_t q, const uint64_t* out_offsets,
+                          uint32_t* out_values, GatherCtx* ctx, cudaStream_t s);
+void gather_release(GatherCtx* ctx, cudaStream_t s);
+
+// Byte-model helper behind hg_probe_stats.
+cudaError_t probe_stats(const Table& t, const void* d_q, uint64_t q, uint64_t* stats, cudaStream_t s);
+
+// Exclusive scan in place over data[0, n) with decoupled look-back; `err` receives DEVERR_TIMEOUT.
+cudaError_t scan_exclusive_u32(uint32_t* data, uint64_t n, uint32_t* err, cudaStream_t s);
+cudaError_t scan_exclusive_u64(uint64_t* data, uint64_t n, uint32_t* err, cudaStream_t s);
+
+}  // namespace hg

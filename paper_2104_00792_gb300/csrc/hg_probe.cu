@@ -1,0 +1,515 @@
+// HashGraph query (Sec. 3.3): hash the probe key, read offset[b] and
+// offset[b + 1], walk keys[offset[b] .. offset[b + 1]) and count (or gather
+// the values of) every key equal to the probe, duplicates included (Sec. 5.5).
+//
+// Buckets are walked by one of three workers, chosen by the bucket's length:
+//   <= WALK_LANE  keys : the query's own lane walks it;
+//   <= WALK_WARP  keys : the whole warp walks it with 16-byte loads;
+//   longer             : the slot goes to a work list, and a second kernel
+//                        splits each listed bucket into LONG_CHUNK-key chunks
+//                        spread over every warp of the GPU, adding partial
+//                        counts atomically.  This keeps a heavily duplicated
+//                        key (millions of copies in one bucket) from holding a
+//                        single warp for milliseconds.
+#include <cstdint>
+
+#include "hg_device.cuh"
+
+namespace hg {
+
+namespace {
+
+constexpr int PROBE_THREADS = 256;
+constexpr uint32_t WALK_LANE = 16;
+constexpr uint32_t WALK_WARP = 8192;
+constexpr uint32_t LONG_CHUNK = 4096;
+constexpr uint32_t COUNT_LONG_CAP = 1u << 22;  // count/join list capacity; overflow -> the warp walks it
+
+enum { OUT_U32 = 0, OUT_U64 = 1, OUT_NONE = 2 };
+enum : uint8_t { CLS_NONE = 0, CLS_LANE = 1, CLS_WARP = 2, CLS_LONG = 3 };
+
+struct LongList {
+    uint32_t* n;             // entries appended (may exceed cap)
+    uint64_t* total_chunks;  // written by k_long_prep
+    uint32_t* slot;          // [cap] query slot of each entry
+    uint64_t* chunk_start;   // [cap] exclusive prefix of chunk counts
+    uint32_t* cursor;        // [cap] gather write cursors (or null)
+    uint32_t cap;
+};
+
+template <typename K>
+__device__ __forceinline__ uint32_t lane_count(const K* __restrict__ keys, uint32_t lo, uint32_t hi, K key) {
+    uint32_t c = 0;
+#pragma unroll 4
+    for (uint32_t p = lo; p < hi; ++p) c += (__ldg(keys + p) == key);
+    return c;
+}
+
+// Number of keys equal to `key` in keys[p0, p1); all 32 lanes call, all get the total.
+template <typename K>
+__device__ __forceinline__ uint32_t warp_count(const K* __restrict__ keys, uint64_t p0, uint64_t p1, K key) {
+    constexpr int VEC = KeyVec<K>::N;
+    const unsigned lane = lane_id();
+    uint32_t c = 0;
+    const uint64_t mis = (reinterpret_cast<uintptr_t>(keys + p0) & 15) / sizeof(K);
+    uint64_t a = p0;
+    if (mis) {
+        uint64_t e = p0 + (VEC - mis);
+        if (e > p1) e = p1;
+        if (a + lane < e) c += (__ldg(keys + a + lane) == key);
+        a = e;
+    }
+    const uint64_t nv = (p1 - a) / VEC;
+    const K* body = keys + a;
+#pragma unroll 4
+    for (uint64_t v = lane; v < nv; v += 32) {
+        const KeyVec<K> kv = load_keys16(body + v * VEC);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) c += (kv.k[j] == key);
+    }
+    a += nv * VEC;
+    if (a + lane < p1) c += (__ldg(keys + a + lane) == key);
+    return __reduce_add_sync(FULL_MASK, c);
+}
+
+// Writes vals[p] for every p in [p0, p1) with keys[p] == key to dst[0, 1, ...] in walk order.
+template <typename K>
+__device__ __forceinline__ void warp_write_matches(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                                   uint64_t p0, uint64_t p1, K key, uint32_t* dst) {
+    const unsigned lane = lane_id();
+    uint64_t w = 0;
+    for (uint64_t base = p0; base < p1; base += 32) {
+        const uint64_t p = base + lane;
+        const bool match = p < p1 && __ldg(keys + p) == key;
+        const unsigned m = __ballot_sync(FULL_MASK, match);
+        if (match) dst[w + __popc(m & lanemask_lt())] = __ldg(vals + p);
+        w += __popc(m);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+    __shared__ T s_part[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5;
+    if (lane_id() == 0) s_part[w] = v;
+    __syncthreads();
+    T r = 0;
+    if (w == 0) {
+        r = (lane_id() < (blockDim.x >> 5)) ? s_part[lane_id()] : (T)0;
+        r = warp_sum(r);
+    }
+    return r;  // valid in thread 0
+}
+
+// One lane's group of up to VEC query slots; all 32 lanes of the warp call it together.
+template <typename K, int OUT, bool GATHER>
+__device__ __forceinline__ void probe_group(const uint64_t (&slot)[KeyVec<K>::N], const bool (&valid)[KeyVec<K>::N],
+                                            const K (&qk)[KeyVec<K>::N], const K* __restrict__ keys,
+                                            const uint32_t* __restrict__ vals, const uint32_t* __restrict__ offs,
+                                            const Hasher& H, uint32_t n_keys, void* counts, const LongList& L,
+                                            const uint64_t* __restrict__ out_offs, uint32_t* out_vals,
+                                            uint64_t& acc) {
+    constexpr int VEC = KeyVec<K>::N;
+    const unsigned lane = lane_id();
+    uint32_t lo[VEC], hi[VEC], cnt[VEC];
+    uint8_t cls[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        lo[j] = hi[j] = 0;
+        if (valid[j]) {
+            const uint32_t b = bucket_of(qk[j], H);
+            lo[j] = __ldg(offs + b);
+            hi[j] = __ldg(offs + b + 1);
+            // offsets of a completed build satisfy lo <= hi <= n; clamp so that a
+            // damaged table can never send a walk outside the keys array
+            hi[j] = min(hi[j], n_keys);
+            lo[j] = min(lo[j], hi[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        const uint32_t len = hi[j] - lo[j];
+        cls[j] = !valid[j] ? CLS_NONE : len <= WALK_LANE ? CLS_LANE : len <= WALK_WARP ? CLS_WARP : CLS_LONG;
+        cnt[j] = 0;
+    }
+    if (!GATHER) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j)
+            if (cls[j] == CLS_LANE) cnt[j] = lane_count(keys, lo[j], hi[j], qk[j]);
+        // long buckets: append to the work list (warp-aggregated); on overflow the warp walks it
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            const unsigned lm = __ballot_sync(FULL_MASK, cls[j] == CLS_LONG);
+            if (lm) {
+                const int leader = __ffs(lm) - 1;
+                uint32_t base = 0;
+                if ((int)lane == leader) base = atomicAdd(L.n, (uint32_t)__popc(lm));
+                base = __shfl_sync(FULL_MASK, base, leader);
+                if (cls[j] == CLS_LONG) {
+                    const uint32_t pos = base + __popc(lm & lanemask_lt());
+                    if (pos < L.cap) L.slot[pos] = (uint32_t)slot[j];
+                    else cls[j] = CLS_WARP;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            if (cls[j] == CLS_LANE) {
+                uint64_t w = out_offs[slot[j]];
+                for (uint32_t p = lo[j]; p < hi[j]; ++p)
+                    if (__ldg(keys + p) == qk[j]) out_vals[w++] = __ldg(vals + p);
+            }
+        }
+    }
+    // medium buckets: the warp walks each one together
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        unsigned mm = __ballot_sync(FULL_MASK, cls[j] == CLS_WARP);
+        while (mm) {
+            const int src = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t l = __shfl_sync(FULL_MASK, lo[j], src);
+            const uint32_t h = __shfl_sync(FULL_MASK, hi[j], src);
+            const K key = __shfl_sync(FULL_MASK, qk[j], src);
+            if (!GATHER) {
+                const uint32_t c = warp_count(keys, l, h, key);
+                if ((int)lane == src) cnt[j] = c;
+            } else {
+                const uint64_t s = __shfl_sync(FULL_MASK, slot[j], src);
+                warp_write_matches(keys, vals, l, h, key, out_vals + out_offs[s]);
+            }
+        }
+    }
+    if (!GATHER) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            if (!valid[j]) continue;
+            if (OUT == OUT_U32) static_cast<uint32_t*>(counts)[slot[j]] = cnt[j];
+            if (OUT == OUT_U64) static_cast<uint64_t*>(counts)[slot[j]] = cnt[j];
+            acc += cnt[j];
+        }
+    }
+}
+
+// Every query slot of qs[0, q): count (OUT_U32 / OUT_U64 into `counts`, the sum
+// into *total when TOTAL) or, when GATHER, write matching values for the
+// non-long slots.  Persistent grid; each lane takes a 16-byte group of slots.
+template <typename K, int OUT, bool TOTAL, bool GATHER>
+__global__ void __launch_bounds__(PROBE_THREADS)
+k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, const K* __restrict__ keys,
+        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
+        uint64_t* total, LongList L, const uint64_t* __restrict__ out_offs, uint32_t* out_vals) {
+    constexpr int VEC = KeyVec<K>::N;
+    const unsigned lane = lane_id();
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t acc = 0;
+    uint64_t slot[VEC];
+    bool valid[VEC];
+    K qk[VEC];
+    for (uint64_t b0 = gw * 32; b0 < nvec; b0 += nw * 32) {
+        const uint64_t v = b0 + lane;
+        const bool ok = v < nvec;
+        KeyVec<K> kv;
+        if (ok) kv = load_keys16(qs + head + v * VEC);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            slot[j] = head + v * VEC + j;
+            valid[j] = ok;
+            qk[j] = ok ? kv.k[j] : (K)0;
+        }
+        probe_group<K, OUT, GATHER>(slot, valid, qk, keys, vals, offs, H, n_keys, counts, L, out_offs, out_vals, acc);
+    }
+    if (gw == 0) {
+        const uint64_t tail0 = head + nvec * VEC;
+        const uint64_t nrem = head + (q - tail0);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            valid[j] = (j == 0) && lane < nrem;
+            slot[j] = lane < head ? lane : tail0 + (lane - head);
+            qk[j] = valid[j] ? qs[slot[j]] : (K)0;
+        }
+        probe_group<K, OUT, GATHER>(slot, valid, qk, keys, vals, offs, H, n_keys, counts, L, out_offs, out_vals, acc);
+    }
+    if (TOTAL) {
+        const uint64_t s = block_sum(acc);
+        if (threadIdx.x == 0 && s) atomicAdd(reinterpret_cast<unsigned long long*>(total), (unsigned long long)s);
+    }
+}
+
+// One block: chunk_start[e] = sum of ceil(len / LONG_CHUNK) over entries before e.
+template <typename K>
+__global__ void __launch_bounds__(1024)
+k_long_prep(const K* __restrict__ qs, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, LongList L) {
+    __shared__ uint64_t s_warp[32];
+    __shared__ uint64_t s_total;
+    const uint32_t n = min(*L.n, L.cap);
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    uint64_t running = 0;
+    for (uint32_t base = 0; base < n; base += blockDim.x) {
+        const uint32_t e = base + threadIdx.x;
+        uint64_t ch = 0;
+        if (e < n) {
+            const uint32_t b = bucket_of(qs[L.slot[e]], H);
+            const uint32_t hi = min(offs[b + 1], n_keys);
+            const uint32_t lo = min(offs[b], hi);
+            ch = (hi - lo + LONG_CHUNK - 1) / LONG_CHUNK;
+        }
+        const uint64_t incl = warp_inclusive_scan(ch);
+        if (lane == 31) s_warp[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const uint64_t wv = lane < (blockDim.x >> 5) ? s_warp[lane] : 0;
+            const uint64_t wi = warp_inclusive_scan(wv);
+            if (lane < (blockDim.x >> 5)) s_warp[lane] = wi - wv;
+            if (lane == 31) s_total = wi;
+        }
+        __syncthreads();
+        if (e < n) L.chunk_start[e] = running + s_warp[w] + incl - ch;
+        running += s_total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *L.total_chunks = running;
+}
+
+// Long buckets, one LONG_CHUNK-key chunk per warp iteration.
+template <typename K, int OUT, bool TOTAL, bool GATHER>
+__global__ void __launch_bounds__(PROBE_THREADS)
+k_long(const K* __restrict__ qs, const K* __restrict__ keys, const uint32_t* __restrict__ vals,
+       const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, LongList L, void* counts, uint64_t* total,
+       const uint64_t* __restrict__ out_offs, uint32_t* out_vals) {
+    const unsigned lane = lane_id();
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t nchunks = *L.total_chunks;
+    const uint32_t n = min(*L.n, L.cap);
+    uint64_t acc = 0;
+    for (uint64_t c = gw; c < nchunks; c += nw) {
+        // entry e: the last with chunk_start[e] <= c
+        uint32_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (L.chunk_start[mid] <= c) lo = mid; else hi = mid;
+        }
+        const uint32_t e = lo;
+        const uint32_t s = L.slot[e];
+        const K key = qs[s];
+        const uint32_t b = bucket_of(key, H);
+        const uint64_t l1 = min(offs[b + 1], n_keys);
+        const uint64_t l0 = min((uint64_t)offs[b], l1);
+        const uint64_t p0 = l0 + (c - L.chunk_start[e]) * LONG_CHUNK;
+        const uint64_t p1 = min(l1, p0 + LONG_CHUNK);
+        const uint32_t cnt = warp_count(keys, p0, p1, key);
+        if (!GATHER) {
+            if (lane == 0 && cnt) {
+                if (OUT == OUT_U32) atomicAdd(static_cast<uint32_t*>(counts) + s, cnt);
+                if (OUT == OUT_U64)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(counts) + s, (unsigned long long)cnt);
+                acc += cnt;
+            }
+        } else if (cnt) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(L.cursor + e, cnt);
+            base = __shfl_sync(FULL_MASK, base, 0);
+            warp_write_matches(keys, vals, p0, p1, key, out_vals + out_offs[s] + base);
+        }
+    }
+    if (TOTAL) {
+        const uint64_t sum = block_sum(acc);
+        if (threadIdx.x == 0 && sum) atomicAdd(reinterpret_cast<unsigned long long*>(total), (unsigned long long)sum);
+    }
+}
+
+template <typename Kern>
+unsigned persistent_grid(Kern kern) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PROBE_THREADS, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return (unsigned)(num_sms() * per_sm);
+}
+
+cudaError_t alloc_list(uint32_t cap, bool with_cursor, cudaStream_t s, void** mem, LongList* L) {
+    const size_t hdr = 16;
+    const size_t bytes = hdr + (size_t)cap * (sizeof(uint32_t) + sizeof(uint64_t) + (with_cursor ? 4 : 0)) + 16;
+    cudaError_t e = dev_alloc(mem, bytes, s);
+    if (e != cudaSuccess) return e;
+    char* p = static_cast<char*>(*mem);
+    L->n = reinterpret_cast<uint32_t*>(p);
+    L->total_chunks = reinterpret_cast<uint64_t*>(p + 8);
+    L->chunk_start = reinterpret_cast<uint64_t*>(p + hdr);
+    L->slot = reinterpret_cast<uint32_t*>(p + hdr + (size_t)cap * 8);
+    L->cursor = with_cursor ? L->slot + cap : nullptr;
+    L->cap = cap;
+    e = cudaMemsetAsync(p, 0, hdr, s);
+    if (e == cudaSuccess && with_cursor) e = cudaMemsetAsync(L->cursor, 0, (size_t)cap * 4, s);
+    return e;
+}
+
+template <typename K>
+void split_vec(const K* qs, uint64_t q, uint64_t* head, uint64_t* nvec) {
+    constexpr int VEC = KeyVec<K>::N;
+    uint64_t h = ((16 - (reinterpret_cast<uintptr_t>(qs) & 15)) & 15) / sizeof(K);
+    if (h > q) h = q;
+    *head = h;
+    *nvec = (q - h) / VEC;
+}
+
+template <typename K, int OUT, bool TOTAL, bool GATHER>
+cudaError_t run_probe(const Table& t, const K* qs, uint64_t q, void* counts, uint64_t* total, const LongList& L,
+                      const uint64_t* out_offs, uint32_t* out_vals, cudaStream_t s) {
+    uint64_t head, nvec;
+    split_vec(qs, q, &head, &nvec);
+    const K* keys = static_cast<const K*>(t.keys);
+    {
+        auto kern = k_probe<K, OUT, TOTAL, GATHER>;
+        unsigned g = persistent_grid(kern);
+        const uint64_t need = (nvec + PROBE_THREADS) / PROBE_THREADS;
+        if (need < g) g = (unsigned)(need < 1 ? 1 : need);
+        launch_begin(GATHER ? "gather" : "probe", s);
+        kern<<<g, PROBE_THREADS, 0, s>>>(qs, q, head, nvec, keys, t.values, t.offsets, t.H, (uint32_t)t.n, counts,
+                                         total, L, out_offs, out_vals);
+        launch_end(GATHER ? "gather" : "probe", s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (!GATHER) {
+        launch_begin("long_prep", s);
+        k_long_prep<K><<<1, 1024, 0, s>>>(qs, t.offsets, t.H, (uint32_t)t.n, L);
+        launch_end("long_prep", s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    auto kern = k_long<K, OUT, TOTAL, GATHER>;
+    launch_begin(GATHER ? "long_gather" : "long", s);
+    kern<<<persistent_grid(kern), PROBE_THREADS, 0, s>>>(qs, keys, t.values, t.offsets, t.H, (uint32_t)t.n, L,
+                                                       counts, total, out_offs, out_vals);
+    launch_end(GATHER ? "long_gather" : "long", s);
+    return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t count_impl(const Table& t, const K* qs, uint64_t q, uint32_t* counts, uint64_t* total, cudaStream_t s) {
+    void* mem = nullptr;
+    LongList L{};
+    const uint32_t cap = (uint32_t)(q < COUNT_LONG_CAP ? q : COUNT_LONG_CAP);
+    cudaError_t e = alloc_list(cap, false, s, &mem, &L);
+    if (e == cudaSuccess) {
+        if (counts && total) e = run_probe<K, OUT_U32, true, false>(t, qs, q, counts, total, L, nullptr, nullptr, s);
+        else if (counts) e = run_probe<K, OUT_U32, false, false>(t, qs, q, counts, nullptr, L, nullptr, nullptr, s);
+        else e = run_probe<K, OUT_NONE, true, false>(t, qs, q, nullptr, total, L, nullptr, nullptr, s);
+    }
+    if (mem) dev_free(mem, s);
+    return e;
+}
+
+// Byte-model helper: stats[0] += sum of walked bucket lengths, stats[1] += the
+// part in buckets longer than WALK_WARP, stats[2] += number of such slots.
+template <typename K>
+__global__ void __launch_bounds__(PROBE_THREADS)
+k_walk_stats(const K* __restrict__ qs, uint64_t q, const uint32_t* __restrict__ offs, Hasher H, uint64_t* stats) {
+    uint64_t w = 0, wl = 0, nl = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < q; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = bucket_of(qs[i], H);
+        const uint32_t len = offs[b + 1] - offs[b];
+        w += len;
+        if (len > WALK_WARP) {
+            wl += len;
+            nl += 1;
+        }
+    }
+    const uint64_t a = block_sum(w);
+    __syncthreads();
+    const uint64_t c = block_sum(wl);
+    __syncthreads();
+    const uint64_t d = block_sum(nl);
+    if (threadIdx.x == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(stats), (unsigned long long)a);
+        atomicAdd(reinterpret_cast<unsigned long long*>(stats + 1), (unsigned long long)c);
+        atomicAdd(reinterpret_cast<unsigned long long*>(stats + 2), (unsigned long long)d);
+    }
+}
+
+}  // namespace
+
+cudaError_t probe_count(const Table& t, const void* d_q, uint64_t q, uint32_t* counts, uint64_t* total,
+                        cudaStream_t s) {
+    if (total) {
+        cudaError_t e = cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (q == 0) return cudaSuccess;
+    if (t.key_bytes == 4) return count_impl<uint32_t>(t, static_cast<const uint32_t*>(d_q), q, counts, total, s);
+    return count_impl<uint64_t>(t, static_cast<const uint64_t*>(d_q), q, counts, total, s);
+}
+
+// Gather keeps its work list between the two phases: phase 1 (counts into
+// out_offsets, then the scan) and phase 2 (the value writes) must agree on
+// which slots are long, so the list is sized for every slot and never overflows.
+
+cudaError_t gather_offsets(const Table& t, const void* d_q, uint64_t q, uint64_t* out_offsets, GatherCtx* ctx,
+                           cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out_offsets + q, 0, sizeof(uint64_t), s);
+    if (e != cudaSuccess || q == 0) return e;
+    LongList L{};
+    e = alloc_list((uint32_t)q, true, s, &ctx->scratch, &L);
+    if (e != cudaSuccess) return e;
+    ctx->slots = q;
+    if (t.key_bytes == 4)
+        e = run_probe<uint32_t, OUT_U64, false, false>(t, static_cast<const uint32_t*>(d_q), q, out_offsets, nullptr,
+                                                       L, nullptr, nullptr, s);
+    else
+        e = run_probe<uint64_t, OUT_U64, false, false>(t, static_cast<const uint64_t*>(d_q), q, out_offsets, nullptr,
+                                                       L, nullptr, nullptr, s);
+    if (e != cudaSuccess) return e;
+    return scan_exclusive_u64(out_offsets, q + 1, t.err, s);
+}
+
+cudaError_t gather_values(const Table& t, const void* d_q, uint64_t q, const uint64_t* out_offsets,
+                          uint32_t* out_values, GatherCtx* ctx, cudaStream_t s) {
+    if (q == 0) return cudaSuccess;
+    // Rebuild the list view over the same scratch (layout fixed by alloc_list).
+    LongList L{};
+    char* p = static_cast<char*>(ctx->scratch);
+    const uint32_t cap = (uint32_t)q;
+    L.n = reinterpret_cast<uint32_t*>(p);
+    L.total_chunks = reinterpret_cast<uint64_t*>(p + 8);
+    L.chunk_start = reinterpret_cast<uint64_t*>(p + 16);
+    L.slot = reinterpret_cast<uint32_t*>(p + 16 + (size_t)cap * 8);
+    L.cursor = L.slot + cap;
+    L.cap = cap;
+    if (t.key_bytes == 4)
+        return run_probe<uint32_t, OUT_NONE, false, true>(t, static_cast<const uint32_t*>(d_q), q, nullptr, nullptr, L,
+                                                          out_offsets, out_values, s);
+    return run_probe<uint64_t, OUT_NONE, false, true>(t, static_cast<const uint64_t*>(d_q), q, nullptr, nullptr, L,
+                                                      out_offsets, out_values, s);
+}
+
+void gather_release(GatherCtx* ctx, cudaStream_t s) {
+    if (ctx->scratch) dev_free(ctx->scratch, s);
+    ctx->scratch = nullptr;
+}
+
+}  // namespace hg
+
+namespace hg {
+
+cudaError_t probe_stats(const Table& t, const void* d_q, uint64_t q, uint64_t* stats, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(stats, 0, 3 * sizeof(uint64_t), s);
+    if (e != cudaSuccess) return e;
+    const uint64_t lim = WALK_WARP;
+    e = cudaMemcpyAsync(stats + 3, &lim, sizeof(lim), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess || q == 0) return e;
+    const unsigned g = (unsigned)(num_sms() * 4);
+    launch_begin("walk_stats", s);
+    if (t.key_bytes == 4)
+        k_walk_stats<uint32_t><<<g, PROBE_THREADS, 0, s>>>(static_cast<const uint32_t*>(d_q), q, t.offsets, t.H, stats);
+    else
+        k_walk_stats<uint64_t><<<g, PROBE_THREADS, 0, s>>>(static_cast<const uint64_t*>(d_q), q, t.offsets, t.H, stats);
+    launch_end("walk_stats", s);
+    return cudaGetLastError();
+}
+
+}  // namespace hg

@@ -1,0 +1,191 @@
+"""CUDA path vs the CPU oracle, element by element, on seeded inputs.
+
+Sizes span several tiles of every kernel and end in ragged tails; the
+workload recipes are the ones the benchmark uses, scaled down.  Offsets,
+counts and totals must be bit-exact; bucket contents and gather segments are
+compared after a canonical sort (the order inside a bucket is free)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests.hg_testutil import assert_same_gather, assert_same_table, from_dev, table_arrays, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2104_00792_gb300 as m
+    return m
+
+
+def _run_all(hg, keys, B, seed, queries, values=None, flags=0, check_gather=True):
+    dt = keys.dtype
+    ref = oracle.build_table(keys, B, seed, values=values, index_values=bool(flags & hg.HG_INDEX_VALUES))
+    dk = to_dev(keys)
+    dv = None if values is None else to_dev(values)
+    dq = to_dev(queries)
+    with hg.hg_build(dk, B, seed, values=dv, flags=flags) as t:
+        o, k, v = table_arrays(hg, t, dt)
+        assert_same_table(o, k, v, ref)
+        # counts and total in one call
+        counts = torch.empty(queries.size, dtype=torch.int32, device="cuda")
+        total = torch.empty(1, dtype=torch.int64, device="cuda")
+        hg.hg_query_count(t, dq, counts, total)
+        want = ref.query_count(queries)
+        got = from_dev(counts, np.uint32).astype(np.uint64)
+        assert np.array_equal(got, want), "counts differ"
+        assert int(from_dev(total, np.uint64)[0]) == int(want.sum())
+        # counts only, then total only (join)
+        counts2 = torch.full((queries.size,), -1, dtype=torch.int32, device="cuda")
+        hg.hg_query_count(t, dq, counts2, None)
+        assert np.array_equal(from_dev(counts2, np.uint32).astype(np.uint64), want)
+        jt = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        hg.hg_join_count(t, dq, jt)
+        assert int(from_dev(jt, np.uint64)[0]) == ref.join_count(queries)
+        if check_gather and v is not None:
+            offs = torch.empty(queries.size + 1, dtype=torch.int64, device="cuda")
+            n_total = int(want.sum())
+            outv = torch.empty(max(n_total, 1), dtype=torch.int32, device="cuda")
+            got_total = hg.hg_query_gather(t, dq, offs, outv)
+            assert got_total == n_total
+            ro, rv = ref.query_gather(queries)
+            assert_same_gather(from_dev(offs, np.uint64), from_dev(outv, np.uint32)[:n_total], ro, rv)
+        hg.hg_sync(t)
+    return ref
+
+
+@pytest.mark.parametrize("B", [1 << 16, 65537, 1, 1000])
+def test_plain_uniform_u32(hg, B):
+    wl = W.plain_uniform(100003, 70001, num_buckets=B)
+    _run_all(hg, wl.keys, B, 0, wl.queries, flags=hg.HG_INDEX_VALUES, check_gather=B != 1)
+
+
+def test_plain_uniform_small_config_full_size(hg):
+    # the small configuration at its stated size: 2^20 keys, 2^20 buckets, 2^20 queries, 50% hits
+    wl = W.plain_uniform(1 << 20, 1 << 20)
+    _run_all(hg, wl.keys, 1 << 20, 0, wl.queries, flags=hg.HG_INDEX_VALUES)
+
+
+@pytest.mark.parametrize("seed", [0, 0xDEADBEEF12345])
+def test_seeded_hash(hg, seed):
+    wl = W.plain_uniform(50001, 40001, num_buckets=4093, salt=3)
+    _run_all(hg, wl.keys, 4093, seed, wl.queries)
+
+
+def test_zipf_duplicates_long_buckets(hg):
+    # top value ~ 2^20 / H(2^14) ~ 1e5 copies: exercises the chunked long-bucket path
+    wl = W.zipf_large(n=1 << 20, num_buckets=1 << 19, q=1 << 20, M=1 << 14)
+    _run_all(hg, wl.keys, 1 << 19, 0, wl.queries, flags=hg.HG_INDEX_VALUES)
+
+
+def test_join_kv_u64_values(hg):
+    wl = W.join_kv(n=(1 << 17) + 3, num_buckets=1 << 16, q=(1 << 16) + 5)
+    _run_all(hg, wl.keys, 1 << 16, 0, wl.queries, values=wl.values)
+
+
+def test_u64_non_power_of_two_buckets(hg):
+    wl = W.join_kv(n=90001, num_buckets=99991, q=70003, salt=2)
+    _run_all(hg, wl.keys, 99991, 7, wl.queries, values=wl.values)
+
+
+def test_all_duplicates_one_bucket(hg):
+    keys = np.full(300001, 0xFFFFFFFF, dtype=np.uint32)
+    keys[::7] = 0
+    queries = np.array([0xFFFFFFFF, 0, 1, 0xFFFFFFFF] * 1001, dtype=np.uint32)
+    _run_all(hg, keys, 1 << 12, 0, queries, flags=hg.HG_INDEX_VALUES)
+
+
+def test_sequential_keys(hg):
+    keys = np.arange(1, (1 << 18) + 1, dtype=np.uint32)
+    queries = np.arange(0, 1 << 18, 3, dtype=np.uint32)
+    _run_all(hg, keys, 1 << 18, 0, queries, flags=hg.HG_INDEX_VALUES)
+
+
+def test_empty_inputs(hg):
+    empty = np.empty(0, dtype=np.uint32)
+    q = np.array([1, 2, 3], dtype=np.uint32)
+    _run_all(hg, empty, 64, 0, q, flags=hg.HG_INDEX_VALUES)
+    wl = W.plain_uniform(1000, 10)
+    _run_all(hg, wl.keys, 1024, 0, empty, flags=hg.HG_INDEX_VALUES)
+
+
+@pytest.mark.parametrize("koff,qoff", [(1, 3), (2, 1), (3, 2)])
+def test_unaligned_inputs(hg, koff, qoff):
+    wl = W.plain_uniform(20011, 30011, num_buckets=8192, salt=5)
+    keys = wl.keys[koff:]
+    queries = wl.queries[qoff:]
+    ref = oracle.build_table(keys, 8192, 0)
+    dk_full = to_dev(wl.keys)
+    dq_full = to_dev(wl.queries)
+    with hg.hg_build(dk_full[koff:], 8192, 0) as t:
+        o, k, v = table_arrays(hg, t, np.uint32)
+        assert_same_table(o, k, v, ref)
+        counts = torch.empty(queries.size, dtype=torch.int32, device="cuda")
+        hg.hg_query_count(t, dq_full[qoff:], counts)
+        assert np.array_equal(from_dev(counts, np.uint32).astype(np.uint64), ref.query_count(queries))
+
+
+def _inv_fmix32(h):
+    M = 1 << 32
+    h ^= h >> 16
+    h = (h * pow(0xC2B2AE35, -1, M)) % M
+    h ^= (h >> 13) ^ (h >> 26)
+    h = (h * pow(0x85EBCA6B, -1, M)) % M
+    h ^= h >> 16
+    return h
+
+
+@pytest.mark.parametrize("B", [3, 7, 65537, 99991, 1000003, 12345679, (1 << 26) - 5])
+def test_remainder_boundaries(hg, B):
+    # keys whose hash is exactly at the edges of the remainder (0, B-1, B, the last
+    # full multiple of B below 2^32, 2^32-1): the kernel's remainder must equal '%'
+    M = 1 << 32
+    last = (M // B) * B
+    targets = {0, 1, B - 1, B, B + 1, 2 * B - 1, last - 1, last, M - 1, M - 2, M - B, (M - 1) // 2}
+    targets = sorted(t for t in targets if 0 <= t < M)
+    keys = [_inv_fmix32(h) for h in targets]
+    assert [oracle.fmix32(k) for k in keys] == targets
+    rng = np.random.default_rng(B)
+    extra = rng.integers(0, M, size=5000, dtype=np.uint64).astype(np.uint32)
+    all_keys = np.concatenate([np.array(keys * 3, dtype=np.uint32), extra])
+    _run_all(hg, all_keys, B, 0, all_keys[::2].copy(), flags=hg.HG_INDEX_VALUES)
+
+
+def test_gather_capacity_two_call_pattern(hg):
+    wl = W.plain_uniform(10000, 5000, num_buckets=10000, hit=0.9)
+    ref = oracle.build_table(wl.keys, 10000, 0, index_values=True)
+    want = int(ref.query_count(wl.queries).sum())
+    with hg.hg_build(to_dev(wl.keys), 10000, 0, flags=hg.HG_INDEX_VALUES) as t:
+        dq = to_dev(wl.queries)
+        offs = torch.empty(wl.queries.size + 1, dtype=torch.int64, device="cuda")
+        small = torch.empty(10, dtype=torch.int32, device="cuda")
+        with pytest.raises(hg.HashGraphError) as ei:
+            hg.hg_query_gather(t, dq, offs, small)
+        assert ei.value.status == hg.HG_ERR_CAPACITY and ei.value.total == want
+        ro, _ = ref.query_gather(wl.queries)
+        assert np.array_equal(from_dev(offs, np.uint64), ro)
+
+
+def test_gather_without_values_is_rejected(hg):
+    wl = W.plain_uniform(1000, 100)
+    with hg.hg_build(to_dev(wl.keys), 1024, 0) as t:
+        offs = torch.empty(101, dtype=torch.int64, device="cuda")
+        with pytest.raises(hg.HashGraphError) as ei:
+            hg.hg_query_gather(t, to_dev(wl.queries), offs, None)
+        assert ei.value.status == hg.HG_ERR_NO_VALUES
+
+
+def test_build_modes_agree(hg):
+    # the direct Algorithm 1 build and the partitioned build give the same table
+    wl = W.zipf_large(n=(1 << 20) + 7, num_buckets=(1 << 20) - 3, q=1 << 10, M=1 << 16)
+    ref = oracle.build_table(wl.keys, (1 << 20) - 3, 0, index_values=True)
+    for flags in (hg.HG_PLAIN_BUILD, hg.HG_PARTITION_BUILD, 0):
+        with hg.hg_build(to_dev(wl.keys), (1 << 20) - 3, 0, flags=flags | hg.HG_INDEX_VALUES) as t:
+            o, k, v = table_arrays(hg, t, np.uint32)
+            assert_same_table(o, k, v, ref)
