@@ -180,7 +180,7 @@ def hg_sync(table: Table, stream=None):
 
 class _DeviceArray:
     def __init__(self, ptr: int, n: int, typestr: str):
-        self.__cuda_array_interface__ = {"data": (ptr or 0, True), "shape": (n,), "typestr": typestr,
+        self.__cuda_array_interface__ = {"data": (ptr or 0, False), "shape": (n,), "typestr": typestr,
                                          "version": 3, "strides": None}
 
 

@@ -247,7 +247,7 @@ hg_status hg_query_count(const hg_table* ht, const void* d_queries, uint64_t q, 
                          uint64_t* d_total, hg_stream_t s) {
     const Table* t = reinterpret_cast<const Table*>(ht);
     if (!t) return fail(HG_ERR_INVALID_ARG, "table is NULL");
-    if (!d_counts && !d_total) return fail(HG_ERR_INVALID_ARG, "d_counts and d_total are both NULL");
+    if (!d_counts && !d_total && q > 0) return fail(HG_ERR_INVALID_ARG, "d_counts and d_total are both NULL");
     if (d_counts && q > 0 && !aligned(d_counts, 4)) return fail(HG_ERR_INVALID_ARG, "d_counts is not 4-byte aligned");
     if (d_total && !aligned(d_total, 8)) return fail(HG_ERR_INVALID_ARG, "d_total is not 8-byte aligned");
     hg_status st = check_queries(t, d_queries, q);

@@ -19,8 +19,8 @@ def _declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2104_00792_gb300 import _build
-    path = _build.build()
+    import __graft_entry__
+    path = __graft_entry__._builder().build()
     return ctypes.CDLL(path), path
 
 
