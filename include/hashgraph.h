@@ -156,6 +156,34 @@ hg_status hg_table_view(const hg_table* t, const void** d_offsets, const void** 
  */
 hg_status hg_probe_stats(const hg_table* t, const void* d_queries, uint64_t q, uint64_t* d_stats, hg_stream_t s);
 
+/*
+ * hg_build_noalloc -- the direct build (hg_build with HG_PLAIN_BUILD) for
+ * callers that cannot allocate device memory.  The paper has no counterpart;
+ * this is a deployment convenience.  Some callers run inside a framework that
+ * owns all device memory (an inference or serving engine with a fixed memory
+ * plan, a plugin that may only use the buffers its host gives it), or must not
+ * allocate once running (a real-time loop, where growing a memory pool
+ * stalls).  They pass every input and output buffer themselves:
+ *   cfg            as for hg_build; only the HG_INDEX_VALUES flag is accepted
+ *   d_keys, d_values, n   as for hg_build
+ *   d_offsets      out: num_buckets + 1 uint32_t (CSR offsets, d_offsets[V] = n)
+ *   d_keys_out     out: n keys grouped by bucket
+ *   d_values_out   out: n uint32_t values, required when the table has values
+ *                  (value_bytes = 4 or HG_INDEX_VALUES), else NULL
+ * The prefix sum's scratch comes from a fixed 64 KiB array inside the library
+ * (held on every GPU that loads it until the process exits), which limits
+ * num_buckets to 2^23 - 1; larger values return HG_ERR_INVALID_ARG.  Nothing
+ * is allocated: no cudaMalloc, cudaMallocAsync or cudaFree is called.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the array: calls whose GPU work overlaps (other streams or threads)
+ * race on it, so order them on one stream.  A kernel that gives up a bounded
+ * wait leaves d_offsets[V] != n, which a caller can check after the stream
+ * syncs.  Asynchronous, like hg_build.
+ */
+hg_status hg_build_noalloc(const hg_config* cfg, const void* d_keys, const void* d_values, uint64_t n,
+                           uint32_t* d_offsets, void* d_keys_out, uint32_t* d_values_out, hg_stream_t s);
+
 /* Number of kernels this process has launched through the library so far. */
 uint64_t hg_launch_count(void);
 

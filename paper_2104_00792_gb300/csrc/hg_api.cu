@@ -75,6 +75,8 @@ std::string g_names_csv;
 
 }  // namespace
 
+void set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
 void launch_begin(const char* name, cudaStream_t s) {
     (void)name;
     if (!g_prof_on) return;

@@ -125,7 +125,57 @@ cudaError_t build_plain(Table& t, const K* keys, const uint32_t* vals, cudaStrea
     return launch(k_scatter<K, 0>);
 }
 
+// The direct build writing into caller-provided arrays, with the scan's scratch
+// supplied by the caller.
+template <typename K>
+cudaError_t build_direct_into_impl(const Hasher& H, const K* keys, const uint32_t* vals, bool index_values,
+                                   uint64_t n, uint64_t B, uint32_t* offsets, K* kout, uint32_t* vout,
+                                   void* scan_scratch, size_t scan_scratch_bytes, uint32_t* err, cudaStream_t s) {
+    constexpr int VEC = KeyVec<K>::N;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(keys);
+    uint64_t head = ((16 - (a & 15)) & 15) / sizeof(K);
+    if (head > n) head = n;
+    const uint64_t nvec = (n - head) / VEC;
+    uint32_t* cnt = offsets + 1;
+    {
+        auto kern = k_hist<K>;
+        const unsigned g = stream_grid(kern, nvec + 1);
+        launch_begin("hist", s);
+        kern<<<g, BUILD_THREADS, 0, s>>>(keys, n, head, nvec, H, cnt);
+        launch_end("hist", s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = scan_exclusive_u32_into(offsets, B + 1, scan_scratch, scan_scratch_bytes, err, s);
+    if (e != cudaSuccess) return e;
+    auto launch = [&](auto kern) {
+        const unsigned g = stream_grid(kern, nvec + 1);
+        launch_begin("scatter", s);
+        kern<<<g, BUILD_THREADS, 0, s>>>(keys, vals, n, head, nvec, H, cnt, kout, vout, err);
+        launch_end("scatter", s);
+        return cudaGetLastError();
+    };
+    if (vals && vout) return launch(k_scatter<K, 1>);
+    if (index_values && vout) return launch(k_scatter<K, 2>);
+    return launch(k_scatter<K, 0>);
+}
+
 }  // namespace
+
+cudaError_t build_direct_into(const Hasher& H, uint32_t key_bytes, const void* keys, const uint32_t* vals,
+                              bool index_values, uint64_t n, uint64_t B, uint32_t* offsets, void* keys_out,
+                              uint32_t* vals_out, void* scan_scratch, size_t scan_scratch_bytes, uint32_t* err,
+                              cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(offsets, 0, (B + 1) * sizeof(uint32_t), s);
+    if (e != cudaSuccess || n == 0) return e;
+    if (key_bytes == 4)
+        return build_direct_into_impl<uint32_t>(H, static_cast<const uint32_t*>(keys), vals, index_values, n, B,
+                                                offsets, static_cast<uint32_t*>(keys_out), vals_out, scan_scratch,
+                                                scan_scratch_bytes, err, s);
+    return build_direct_into_impl<uint64_t>(H, static_cast<const uint64_t*>(keys), vals, index_values, n, B, offsets,
+                                            static_cast<uint64_t*>(keys_out), vals_out, scan_scratch,
+                                            scan_scratch_bytes, err, s);
+}
 
 cudaError_t build_table(Table& t, const void* d_keys, const void* d_values, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(t.offsets, 0, (t.B + 1) * sizeof(uint32_t), s);

@@ -47,6 +47,9 @@ struct Table {
     uint32_t* err = nullptr;      // device error word
 };
 
+// Sets the message hg_last_error() returns on the calling thread.
+void set_error_message(const char* msg);
+
 // Stream-ordered allocation from the device's default memory pool.
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);
@@ -81,5 +84,19 @@ cudaError_t probe_stats(const Table& t, const void* d_q, uint64_t q, uint64_t* s
 // Exclusive scan in place over data[0, n) with decoupled look-back; `err` receives DEVERR_TIMEOUT.
 cudaError_t scan_exclusive_u32(uint32_t* data, uint64_t n, uint32_t* err, cudaStream_t s);
 cudaError_t scan_exclusive_u64(uint64_t* data, uint64_t n, uint32_t* err, cudaStream_t s);
+
+// The same scan with caller-provided scratch (16-byte aligned, at least
+// scan_u32_scratch_bytes(data, n) bytes); allocates nothing.
+size_t scan_u32_scratch_bytes(const uint32_t* data, uint64_t n);
+cudaError_t scan_exclusive_u32_into(uint32_t* data, uint64_t n, void* scratch, size_t scratch_bytes, uint32_t* err,
+                                    cudaStream_t s);
+
+// Direct Algorithm 1 build into caller-provided CSR arrays, scan scratch supplied
+// by the caller; allocates nothing.  vals may be null; index_values stores input
+// positions as values (vals_out required then).
+cudaError_t build_direct_into(const Hasher& H, uint32_t key_bytes, const void* keys, const uint32_t* vals,
+                              bool index_values, uint64_t n, uint64_t B, uint32_t* offsets, void* keys_out,
+                              uint32_t* vals_out, void* scan_scratch, size_t scan_scratch_bytes, uint32_t* err,
+                              cudaStream_t s);
 
 }  // namespace hg

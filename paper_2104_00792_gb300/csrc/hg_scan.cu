@@ -175,7 +175,44 @@ cudaError_t launch_scan(T* data, uint64_t n, uint32_t* err, cudaStream_t s) {
     return e;
 }
 
+// Same kernel, scratch supplied by the caller (no allocation).  The flags and
+// the tile counter are cleared here; the aggregate/prefix slots need no clearing.
+template <typename T, int V, int ROWS>
+cudaError_t launch_scan_into(T* data, uint64_t n, void* scratch, size_t scratch_bytes, uint32_t* err,
+                             cudaStream_t s) {
+    constexpr uint64_t TILE = (uint64_t)SCAN_WARPS * ROWS * 32 * V;
+    const uint64_t ntiles = (n + TILE - 1) / TILE;
+    const size_t flag_bytes = ((ntiles + 1) * sizeof(uint32_t) + 15) & ~size_t(15);
+    if (flag_bytes + 2 * ntiles * sizeof(T) > scratch_bytes || (reinterpret_cast<uintptr_t>(scratch) & 15))
+        return cudaErrorInvalidValue;
+    uint32_t* flags = static_cast<uint32_t*>(scratch);
+    uint32_t* ctr = flags + ntiles;
+    T* aggs = reinterpret_cast<T*>(static_cast<char*>(scratch) + flag_bytes);
+    T* pres = aggs + ntiles;
+    cudaError_t e = cudaMemsetAsync(flags, 0, (ntiles + 1) * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    launch_begin("scan", s);
+    k_scan_exclusive<T, V, ROWS><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(data, n, flags, aggs, pres, ctr, err);
+    launch_end("scan", s);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t scan_u32_scratch_bytes(const uint32_t* data, uint64_t n) {
+    const uint64_t tile = (reinterpret_cast<uintptr_t>(data) & 15) == 0 ? (uint64_t)SCAN_WARPS * 4 * 32 * 4
+                                                                          : (uint64_t)SCAN_WARPS * 8 * 32 * 1;
+    const uint64_t ntiles = (n + tile - 1) / tile;
+    return (((ntiles + 1) * sizeof(uint32_t) + 15) & ~size_t(15)) + 2 * ntiles * sizeof(uint32_t);
+}
+
+cudaError_t scan_exclusive_u32_into(uint32_t* data, uint64_t n, void* scratch, size_t scratch_bytes, uint32_t* err,
+                                    cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if ((reinterpret_cast<uintptr_t>(data) & 15) == 0)
+        return launch_scan_into<uint32_t, 4, 4>(data, n, scratch, scratch_bytes, err, s);
+    return launch_scan_into<uint32_t, 1, 8>(data, n, scratch, scratch_bytes, err, s);
+}
 
 cudaError_t scan_exclusive_u32(uint32_t* data, uint64_t n, uint32_t* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
