@@ -177,7 +177,17 @@ cudaError_t build_direct_into(const Hasher& H, uint32_t key_bytes, const void* k
                                             scan_scratch_bytes, err, s);
 }
 
+// The partitioned build (Sec. 3.2 binning) pays off once the offsets array no
+// longer fits in L2; forced either way by HG_PARTITION_BUILD / HG_PLAIN_BUILD.
+static bool use_partition(const Table& t) {
+    if (t.flags & HG_PLAIN_BUILD) return false;
+    if (!partition_supported(t.B)) return false;
+    if (t.flags & HG_PARTITION_BUILD) return true;
+    return t.B >= (1ull << 21);
+}
+
 cudaError_t build_table(Table& t, const void* d_keys, const void* d_values, cudaStream_t s) {
+    if (t.n > 0 && use_partition(t)) return build_partitioned(t, d_keys, d_values, s);
     cudaError_t e = cudaMemsetAsync(t.offsets, 0, (t.B + 1) * sizeof(uint32_t), s);
     if (e != cudaSuccess || t.n == 0) return e;
     const uint32_t* vals = static_cast<const uint32_t*>(d_values);

@@ -61,6 +61,9 @@ int num_sms();
 
 // Build (Algorithm 1): fills t.offsets, t.keys, t.values.  Returns a CUDA error.
 cudaError_t build_table(Table& t, const void* d_keys, const void* d_values, cudaStream_t s);
+// The partitioned build (Sec. 3.2 binning); requires partition_supported(B).
+bool partition_supported(uint64_t B);
+cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values, cudaStream_t s);
 
 // Probe entry points.  Return a CUDA error.
 //   counts: u32 per slot (may be null); total: u64 sum (may be null).

@@ -24,9 +24,18 @@ def hg():
     return m
 
 
-def _run_all(hg, keys, B, seed, queries, values=None, flags=0, check_gather=True):
-    dt = keys.dtype
+def _run_all(hg, keys, B, seed, queries, values=None, flags=0, check_gather=True,
+             modes=("plain", "partition")):
+    """Both builds (direct Algorithm 1 and the partitioned one) against the oracle."""
     ref = oracle.build_table(keys, B, seed, values=values, index_values=bool(flags & hg.HG_INDEX_VALUES))
+    for mode in modes:
+        extra = hg.HG_PLAIN_BUILD if mode == "plain" else hg.HG_PARTITION_BUILD
+        _run_one(hg, ref, keys, B, seed, queries, values, flags | extra, check_gather)
+    return ref
+
+
+def _run_one(hg, ref, keys, B, seed, queries, values, flags, check_gather):
+    dt = keys.dtype
     dk = to_dev(keys)
     dv = None if values is None else to_dev(values)
     dq = to_dev(queries)
@@ -57,7 +66,6 @@ def _run_all(hg, keys, B, seed, queries, values=None, flags=0, check_gather=True
             ro, rv = ref.query_gather(queries)
             assert_same_gather(from_dev(offs, np.uint64), from_dev(outv, np.uint32)[:n_total], ro, rv)
         hg.hg_sync(t)
-    return ref
 
 
 @pytest.mark.parametrize("B", [1 << 16, 65537, 1, 1000])
@@ -123,12 +131,13 @@ def test_unaligned_inputs(hg, koff, qoff):
     ref = oracle.build_table(keys, 8192, 0)
     dk_full = to_dev(wl.keys)
     dq_full = to_dev(wl.queries)
-    with hg.hg_build(dk_full[koff:], 8192, 0) as t:
-        o, k, v = table_arrays(hg, t, np.uint32)
-        assert_same_table(o, k, v, ref)
-        counts = torch.empty(queries.size, dtype=torch.int32, device="cuda")
-        hg.hg_query_count(t, dq_full[qoff:], counts)
-        assert np.array_equal(from_dev(counts, np.uint32).astype(np.uint64), ref.query_count(queries))
+    for flags in (hg.HG_PLAIN_BUILD, hg.HG_PARTITION_BUILD):
+        with hg.hg_build(dk_full[koff:], 8192, 0, flags=flags) as t:
+            o, k, v = table_arrays(hg, t, np.uint32)
+            assert_same_table(o, k, v, ref)
+            counts = torch.empty(queries.size, dtype=torch.int32, device="cuda")
+            hg.hg_query_count(t, dq_full[qoff:], counts)
+            assert np.array_equal(from_dev(counts, np.uint32).astype(np.uint64), ref.query_count(queries))
 
 
 def _inv_fmix32(h):
@@ -189,3 +198,26 @@ def test_build_modes_agree(hg):
         with hg.hg_build(to_dev(wl.keys), (1 << 20) - 3, 0, flags=flags | hg.HG_INDEX_VALUES) as t:
             o, k, v = table_arrays(hg, t, np.uint32)
             assert_same_table(o, k, v, ref)
+
+
+def test_two_pass_partition_with_hot_buckets(hg):
+    # 2^21 + 5 buckets: 257 bins, so both partition passes run; Zipf keys put
+    # tens of thousands of copies in single buckets (big bins, hot buckets)
+    B = (1 << 21) + 5
+    wl = W.zipf_large(n=(1 << 21) + 3, num_buckets=B, q=1 << 16, M=1 << 15, salt=4)
+    _run_all(hg, wl.keys, B, 0, wl.queries, flags=hg.HG_INDEX_VALUES, check_gather=False)
+
+
+def test_partition_u64_values_many_bins(hg):
+    B = 1 << 23
+    wl = W.join_kv(n=1 << 22, num_buckets=B, q=1 << 15, salt=6)
+    _run_all(hg, wl.keys, B, 0, wl.queries, values=wl.values, check_gather=False, modes=("partition",))
+
+
+def test_partition_many_hot_buckets_in_one_bin(hg):
+    # more hot buckets in one bin than the staging map holds: the fallback path
+    rng = np.random.default_rng(3)
+    vals = rng.integers(0, 2**32, size=400, dtype=np.uint64).astype(np.uint32)
+    keys = np.repeat(vals, 80)
+    rng.shuffle(keys)
+    _run_all(hg, keys, 4096, 0, vals[::3].copy(), flags=hg.HG_INDEX_VALUES, check_gather=False)
