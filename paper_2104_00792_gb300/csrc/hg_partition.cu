@@ -39,7 +39,7 @@ constexpr uint32_t RADIX = 128;             // digits per partition pass
 constexpr uint32_t MAX_BINS = RADIX * RADIX;
 constexpr int PASS_THREADS = 256;
 constexpr int LOCAL_THREADS = 512;
-constexpr uint32_t CHUNK = 1u << 19;        // keys per reduce-then-scan chunk
+constexpr uint32_t CHUNK = 1u << 16;        // keys per reduce-then-scan chunk
 constexpr uint32_t MAX_HOT = 256;           // buckets per bin that may bypass the staging buffer
 constexpr size_t LOCAL_STAGE_BYTES = 72 * 1024;
 constexpr uint32_t HUGE_T = 1u << 18;       // bins with more keys are split over many CTAs
@@ -86,9 +86,9 @@ __device__ __forceinline__ uint32_t bin_of(K k, const Hasher& H) {
 }
 
 // Calls f(i, key, value, mask) for every i in [s0, s1): the 16-byte aligned body
-// two vectors per thread at a time, the few elements around it by warp 0.
+// U vectors per thread at a time, the few elements around it by warp 0.
 // `mask` = lanes of the warp calling f together.  HV: also load in_v[i].
-template <typename K, bool HV, typename F>
+template <typename K, bool HV, int U = 2, typename F>
 __device__ __forceinline__ void block_for_range(const K* __restrict__ in, const uint32_t* __restrict__ in_v,
                                                 uint64_t s0, uint64_t s1, F&& f) {
     constexpr int VEC = KeyVec<K>::N;
@@ -98,12 +98,12 @@ __device__ __forceinline__ void block_for_range(const K* __restrict__ in, const 
     const uint64_t hend = mis ? min(s1, s0 + (VEC - mis)) : s0;
     const uint64_t nv = s1 > hend ? (s1 - hend) / VEC : 0;
     const uint64_t tail0 = hend + nv * VEC;
-    for (uint64_t g0 = (threadIdx.x & ~31u) * 2; g0 < nv; g0 += 2ull * nt) {
-        KeyVec<K> kv[2];
-        uint32_t vv[2][VEC];
-        bool ok[2];
+    for (uint64_t g0 = (threadIdx.x & ~31u) * U; g0 < nv; g0 += (uint64_t)U * nt) {
+        KeyVec<K> kv[U];
+        uint32_t vv[U][VEC];
+        bool ok[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const uint64_t g = g0 + u * 32 + lane;
             ok[u] = g < nv;
             if (ok[u]) {
@@ -120,7 +120,7 @@ __device__ __forceinline__ void block_for_range(const K* __restrict__ in, const 
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const unsigned m = __ballot_sync(FULL_MASK, ok[u]);
             if (ok[u]) {
                 const uint64_t e = hend + (g0 + u * 32 + lane) * VEC;
@@ -196,7 +196,7 @@ k_part_count(const K* __restrict__ keys, uint64_t n, Hasher H, uint32_t P, uint3
         for (uint32_t i = threadIdx.x; i < RADIX; i += blockDim.x) s_dig[i] = 0;
         __syncthreads();
         const uint64_t lo = (uint64_t)c * CHUNK, hi = min(n, lo + CHUNK);
-        block_for_range<K, false>(keys, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned m) {
+        block_for_range<K, false, 4>(keys, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned m) {
             const uint32_t b = bin_of(k, H);
             smem_add1(s_hist, b, m);
             smem_add1(s_dig, b >> dig_shift, m);
@@ -221,7 +221,7 @@ k_chunk_count(const K* __restrict__ in, Hasher H, ChunkMap cm, const Plan* __res
     chunk_range(cm, c, seg, first, lo, hi);
     for (uint32_t i = threadIdx.x; i < RADIX; i += blockDim.x) s_dig[i] = 0;
     __syncthreads();
-    block_for_range<K, false>(in, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned m) {
+    block_for_range<K, false, 4>(in, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned m) {
         smem_add1(s_dig, bin_of(k, H) & (RADIX - 1), m);
     });
     __syncthreads();
@@ -338,26 +338,23 @@ k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uin
     }
 }
 
-// One CTA of 1024 threads (8 groups x 128 digits).  On return cnt[c][d] holds
-// the start of digit d's run of chunk c: digit_start(seg(c), d) + the number of
-// keys with digit d in earlier chunks of the same segment.  digit_start =
-// bin_start[d * dig_mul] for a single-segment pass, bin_start[s * P2 + d] for
-// a segmented one.  pref (same shape) receives the plain prefix over all chunks.
+// One CTA of 1024 threads per digit d.  On return cnt[c][d] holds the start of
+// digit d's run of chunk c: digit_start(seg(c), d) + the number of keys with
+// digit d in earlier chunks of the same segment.  digit_start = bin_start[d *
+// dig_mul] for a single-segment pass, bin_start[s * P2 + d] for a segmented
+// one.  pref (same shape) receives the plain prefix over all chunks.
 __global__ void __launch_bounds__(1024)
 k_chunk_scan(uint32_t* cnt, uint32_t* pref, ChunkMap cm, uint32_t nch_host, const Plan* __restrict__ plan, uint32_t R,
              uint32_t dig_mul) {
-    __shared__ uint32_t s_part[8][RADIX];
+    __shared__ uint32_t s_warp[33];
     const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
-    const uint32_t d = threadIdx.x & (RADIX - 1);
-    const uint32_t g = threadIdx.x >> 7;
-    const uint32_t L = (nch + 7) / 8;
-    const uint32_t c0 = min(nch, g * L), c1 = min(nch, c0 + L);
+    const uint32_t d = blockIdx.x;
+    const uint32_t per = (nch + blockDim.x - 1) / blockDim.x;
+    const uint32_t c0 = min(nch, threadIdx.x * per), c1 = min(nch, c0 + per);
     uint32_t sum = 0;
     for (uint32_t c = c0; c < c1; ++c) sum += cnt[(uint64_t)c * RADIX + d];
-    s_part[g][d] = sum;
-    __syncthreads();
-    uint32_t run = 0;
-    for (uint32_t q = 0; q < g; ++q) run += s_part[q][d];
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan<uint32_t>(sum, s_warp, &tot);
     for (uint32_t c = c0; c < c1; ++c) {
         pref[(uint64_t)c * RADIX + d] = run;
         run += cnt[(uint64_t)c * RADIX + d];
@@ -379,7 +376,36 @@ k_chunk_scan(uint32_t* cnt, uint32_t* pref, ChunkMap cm, uint32_t nch_host, cons
 
 // ------------------------------------------------------------ downsweep --
 // One CTA per chunk: tiles in order; run[d] = where the chunk's next key with
-// digit d goes.  Shared memory: keys[TILE] | payload[TILE] | digit[TILE] (u8).
+// digit d goes.  Element li of a tile is held by thread (li / 4) % 256, slot
+// (li / 1024) * 4 + li % 4, so each thread's four consecutive keys come from one
+// 16-byte load when the chunk is aligned.  The next tile's keys are loaded
+// while the current one is ranked, staged and written.
+// Shared memory: keys[TILE] | payload[TILE] | destination[TILE].
+template <typename K, int PM>
+__device__ __forceinline__ void load_tile(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_t t0,
+                                          uint32_t cnt_tile, bool vec, K (&k)[PassCfg<K>::IPT],
+                                          uint32_t (&v)[PassCfg<K>::IPT]) {
+    constexpr int IPT = PassCfg<K>::IPT;
+    constexpr int G = 16 / sizeof(K);  // keys per 16-byte group
+#pragma unroll
+    for (int jj = 0; jj < IPT / G; ++jj) {
+        const uint32_t li0 = (threadIdx.x + jj * PASS_THREADS) * G;
+        if (vec && li0 + G <= cnt_tile) {
+            const KeyVec<K> kv = load_keys16(in + t0 + li0);
+#pragma unroll
+            for (int u = 0; u < G; ++u) k[jj * G + u] = kv.k[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < G; ++u) k[jj * G + u] = li0 + u < cnt_tile ? in[t0 + li0 + u] : (K)0;
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            if (PM == 1) v[jj * G + u] = li0 + u < cnt_tile ? in_v[t0 + li0 + u] : 0u;
+            if (PM == 2) v[jj * G + u] = (uint32_t)(t0 + li0 + u);
+        }
+    }
+}
+
 template <typename K, int PM>
 __global__ void __launch_bounds__(PASS_THREADS, 3)
 k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_t n, Hasher H, uint32_t dig_shift,
@@ -388,10 +414,11 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             uint32_t* err) {
     constexpr int IPT = PassCfg<K>::IPT;
     constexpr int TILE = PassCfg<K>::TILE;
+    constexpr int G = 16 / sizeof(K);
     extern __shared__ __align__(16) unsigned char smem[];
     K* s_keys = reinterpret_cast<K*>(smem);
-    uint32_t* s_pay = reinterpret_cast<uint32_t*>(smem + TILE * sizeof(K));
-    uint8_t* s_dig = reinterpret_cast<uint8_t*>(smem + TILE * sizeof(K) + (PM ? TILE * 4 : 0));
+    uint32_t* s_dst = reinterpret_cast<uint32_t*>(smem + TILE * sizeof(K));
+    uint32_t* s_pay = s_dst + TILE;
     __shared__ uint32_t s_cnt[RADIX], s_loc[RADIX], s_base[RADIX], s_run[RADIX], s_warp[4];
 
     const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
@@ -400,28 +427,22 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
     uint32_t seg, first;
     uint64_t lo, hi;
     chunk_range(cm, c, seg, first, lo, hi);
+    const bool vec = (reinterpret_cast<uintptr_t>(in + lo) & 15) == 0;
     for (uint32_t d = threadIdx.x; d < RADIX; d += blockDim.x) {
         s_cnt[d] = 0;
         s_run[d] = d < R ? chunk_base[(uint64_t)c * RADIX + d] : 0u;
     }
     __syncthreads();
 
+    K k[IPT];
+    uint32_t v[IPT];
+    if (lo < hi) load_tile<K, PM>(in, in_v, lo, (uint32_t)min((uint64_t)TILE, hi - lo), vec, k, v);
     for (uint64_t t0 = lo; t0 < hi; t0 += TILE) {
         const uint32_t cnt_tile = (uint32_t)min((uint64_t)TILE, hi - t0);
-        K k[IPT];
-        uint32_t v[IPT];
         uint32_t dr[IPT];  // rank << 8 | digit
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
-            const uint32_t li = threadIdx.x + j * PASS_THREADS;
-            const bool ok = li < cnt_tile;
-            k[j] = ok ? in[t0 + li] : (K)0;
-            if (PM == 1) v[j] = ok ? in_v[t0 + li] : 0u;
-            if (PM == 2) v[j] = (uint32_t)(t0 + li);
-        }
-#pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            const uint32_t li = threadIdx.x + j * PASS_THREADS;
+            const uint32_t li = (threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G);
             const bool ok = li < cnt_tile;
             const unsigned m = __ballot_sync(FULL_MASK, ok);
             dr[j] = 0;
@@ -452,19 +473,22 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
-            const uint32_t li = threadIdx.x + j * PASS_THREADS;
+            const uint32_t li = (threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G);
             if (li < cnt_tile) {
                 const uint32_t d = dr[j] & 0xffu;
-                const uint32_t pos = s_loc[d] + (dr[j] >> 8);
+                const uint32_t r = dr[j] >> 8;
+                const uint32_t pos = s_loc[d] + r;
                 s_keys[pos] = k[j];
+                s_dst[pos] = s_base[d] + r;
                 if (PM) s_pay[pos] = v[j];
-                s_dig[pos] = (uint8_t)d;
             }
         }
         __syncthreads();
+        // prefetch the next tile while this one is written out
+        const uint64_t t1 = t0 + TILE;
+        if (t1 < hi) load_tile<K, PM>(in, in_v, t1, (uint32_t)min((uint64_t)TILE, hi - t1), vec, k, v);
         for (uint32_t i = threadIdx.x; i < cnt_tile; i += PASS_THREADS) {
-            const uint32_t d = s_dig[i];
-            const uint64_t dst = (uint64_t)s_base[d] + (i - s_loc[d]);
+            const uint32_t dst = s_dst[i];
             if (dst < n) {
                 out[dst] = s_keys[i];
                 if (PM) out_v[dst] = s_pay[i];
@@ -777,7 +801,7 @@ size_t local_smem_bytes(size_t key_bytes, bool hv) {
 template <typename K>
 size_t pass_smem_bytes(bool payload) {
     constexpr int TILE = PassCfg<K>::TILE;
-    return (size_t)TILE * sizeof(K) + (payload ? (size_t)TILE * 4 : 0) + TILE;
+    return (size_t)TILE * sizeof(K) + (size_t)TILE * 4 + (payload ? (size_t)TILE * 4 : 0);
 }
 
 template <typename Kern>
@@ -894,7 +918,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     // 3a. first pass: chunk bases, then the downsweep
     if (e == cudaSuccess) {
         launch_begin("part_plan", s);
-        k_chunk_scan<<<1, 1024, 0, s>>>(cnt_a, pref, cm_a, nch_a, plan, R1, two ? P2 : 1u);
+        k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt_a, pref, cm_a, nch_a, plan, R1, two ? P2 : 1u);
         launch_end("part_plan", s);
         e = cudaGetLastError();
     }
@@ -921,7 +945,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
         e = cudaGetLastError();
         if (e == cudaSuccess) {
             launch_begin("part_plan", s);
-            k_chunk_scan<<<1, 1024, 0, s>>>(cnt_b, pref, cm_b, 0u, plan, P2, 1u);
+            k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt_b, pref, cm_b, 0u, plan, P2, 1u);
             launch_end("part_plan", s);
             e = cudaGetLastError();
         }
