@@ -39,7 +39,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--log2n", type=int, default=28, help="log2 of build keys (queries equal, buckets half)")
-    p.add_argument("--cpu-sample-log2", type=int, default=24)
+    p.add_argument("--cpu-sample-log2", type=int, default=27)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -300,16 +300,28 @@ def run_ours(args, rank, world, local_rank):
 
     value = world * (N + Q) / (ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    # algorithmic bytes per launch of each kernel (k = 4 key bytes, v = 0, o = 4 offset bytes)
+    # Algorithmic bytes per launch of each kernel (k = 4 key bytes, v = 0 value
+    # bytes, o = 4 offset bytes; W = keys walked by all bucket walks, W_long =
+    # the part walked by the chunked long-bucket kernel).  Partition passes move
+    # every key once in each direction; counting passes read every key once.
     k, o = 4, 4
     W, WL = walk["walked"], walk["walked_long"]
     model = {
-        "hist": k * N + 4 * B,
+        "hist": k * N + 4 * B,                        # direct build: keys + counter writes
         "scan": 4 * (B + 1) + o * (B + 1),
         "scatter": 2 * k * N + o * B,
+        "part_hist": k * N,                           # bin histogram + first-pass chunk counts
+        "chunk_count": k * N,                         # second-pass chunk counts
+        "part_scatter": 2 * k * N,                    # one partition pass
+        "bin_build": 2 * k * N + o * (B + 1),         # per-bin counting sort: keys in, keys + offsets out
+        "q_part_count": k * Q,
+        "q_partition": 2 * k * Q + 4 * Q,             # queries grouped + their positions
         "probe": k * Q + 8 * Q + k * (W - WL) + 4 * Q,
         "long": k * WL,
+        "unpermute": 12 * Q,                          # positions, gathered counts, counts out
     }
+    # the method's own byte model for the whole step (build + probe; offsets 4 B)
+    step_model = (3 * k) * N + 16 * B + (k + 12) * Q + k * W
     per_kernel = {}
     for name, (n_launch, tot_ms) in prof.items():
         if n_launch:
@@ -321,7 +333,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max((n for n in per_kernel if n in model), key=lambda n: per_kernel[n]["share"])
     d = per_kernel[dom]
     achieved = model[dom] / (d["ms_per_launch"] * 1e-3) / 1e9
-    step_bytes = sum(model.values())
+    step_bytes = step_model
     clocks = sampler.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -41,7 +41,8 @@ std::atomic<uint64_t> g_launches{0};
 
 // ---- per-kernel event timing (diagnostics) ----
 const char* const kKernelNames[] = {"hist", "scan", "scatter", "probe", "long_prep", "long", "gather",
-                                    "long_gather", "walk_stats", "part_hist", "part_plan", "part_scatter", "huge_count", "huge_scan", "bin_build"};
+                                    "long_gather", "walk_stats", "part_hist", "part_plan", "chunk_scan", "chunk_count", "part_scatter", "huge_count",
+                                    "huge_scan", "bin_build", "q_part_count", "q_partition", "unpermute"};
 struct ProfRecord {
     const char* name;
     cudaEvent_t start, stop;

@@ -65,6 +65,13 @@ cudaError_t build_table(Table& t, const void* d_keys, const void* d_values, cuda
 bool partition_supported(uint64_t B);
 cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values, cudaStream_t s);
 
+// Queries grouped by coarse bucket range so that each range's slice of the
+// table is probed while it sits in L2.  probe_partition_plan decides whether
+// it pays off and picks the range width (digit = bin >> shift, ncoarse ranges).
+bool probe_partition_plan(const Table& t, uint64_t q, uint32_t* shift, uint32_t* ncoarse);
+cudaError_t partition_queries(const Table& t, const void* d_q, uint64_t q, uint32_t shift, uint32_t ncoarse,
+                              void* q_sorted, uint32_t* pos, cudaStream_t s);
+
 // Probe entry points.  Return a CUDA error.
 //   counts: u32 per slot (may be null); total: u64 sum (may be null).
 cudaError_t probe_count(const Table& t, const void* d_q, uint64_t q, uint32_t* counts, uint64_t* total,

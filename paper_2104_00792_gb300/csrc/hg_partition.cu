@@ -183,30 +183,37 @@ __device__ __forceinline__ void chunk_range(const ChunkMap& cm, uint32_t c, uint
 }
 
 // ---------------------------------------------------------------- count --
-// Bin histogram (shared memory per CTA, flushed once) and, per chunk of the
-// input, the counts of the first pass's digit (bin >> dig_shift).
-template <typename K>
+// Bin histogram (shared memory per CTA, flushed once; BINS only) and, per
+// chunk of the input, the counts of the first pass's digit (bin >> dig_shift);
+// digit totals are also added into digit_total when it is given.
+template <typename K, bool BINS>
 __global__ void __launch_bounds__(PASS_THREADS)
 k_part_count(const K* __restrict__ keys, uint64_t n, Hasher H, uint32_t P, uint32_t dig_shift, uint32_t R,
-             uint32_t nch, uint32_t* bin_count, uint32_t* chunk_cnt) {
+             uint32_t nch, uint32_t* bin_count, uint32_t* chunk_cnt, uint32_t* digit_total) {
     extern __shared__ uint32_t s_hist[];
     __shared__ uint32_t s_dig[RADIX];
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_hist[i] = 0;
+    if (BINS)
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_hist[i] = 0;
     for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
         for (uint32_t i = threadIdx.x; i < RADIX; i += blockDim.x) s_dig[i] = 0;
         __syncthreads();
         const uint64_t lo = (uint64_t)c * CHUNK, hi = min(n, lo + CHUNK);
         block_for_range<K, false, 4>(keys, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned m) {
             const uint32_t b = bin_of(k, H);
-            smem_add1(s_hist, b, m);
+            if (BINS) smem_add1(s_hist, b, m);
             smem_add1(s_dig, b >> dig_shift, m);
         });
         __syncthreads();
-        for (uint32_t d = threadIdx.x; d < R; d += blockDim.x) chunk_cnt[(uint64_t)c * RADIX + d] = s_dig[d];
+        for (uint32_t d = threadIdx.x; d < R; d += blockDim.x) {
+            chunk_cnt[(uint64_t)c * RADIX + d] = s_dig[d];
+            if (digit_total && s_dig[d]) atomicAdd(digit_total + d, s_dig[d]);
+        }
     }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
-        if (s_hist[i]) atomicAdd(bin_count + i, s_hist[i]);
+    if (BINS) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(bin_count + i, s_hist[i]);
+    }
 }
 
 // Second-pass chunk counts: digit = bin & (RADIX - 1) inside each chunk's segment.
@@ -345,7 +352,7 @@ k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uin
 // one.  pref (same shape) receives the plain prefix over all chunks.
 __global__ void __launch_bounds__(1024)
 k_chunk_scan(uint32_t* cnt, uint32_t* pref, ChunkMap cm, uint32_t nch_host, const Plan* __restrict__ plan, uint32_t R,
-             uint32_t dig_mul) {
+             uint32_t dig_mul, const uint32_t* __restrict__ digit_total) {
     __shared__ uint32_t s_warp[33];
     const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
     const uint32_t d = blockIdx.x;
@@ -367,8 +374,12 @@ k_chunk_scan(uint32_t* cnt, uint32_t* pref, ChunkMap cm, uint32_t nch_host, cons
         chunk_range(cm, c, seg, first, lo, hi);
         uint32_t start = 0;
         if (d < R) {
-            const uint32_t bin = cm.segmented ? seg * cm.P2 + d : d * dig_mul;
-            start = cm.bin_start[min(bin, cm.P)];
+            if (digit_total) {
+                for (uint32_t q = 0; q < d; ++q) start += digit_total[q];
+            } else {
+                const uint32_t bin = cm.segmented ? seg * cm.P2 + d : d * dig_mul;
+                start = cm.bin_start[min(bin, cm.P)];
+            }
         }
         cnt[(uint64_t)c * RADIX + d] = start + pref[(uint64_t)c * RADIX + d] - pref[(uint64_t)first * RADIX + d];
     }
@@ -406,12 +417,12 @@ __device__ __forceinline__ void load_tile(const K* __restrict__ in, const uint32
     }
 }
 
-template <typename K, int PM>
+template <typename K, int PM, bool POS = false>
 __global__ void __launch_bounds__(PASS_THREADS, 3)
 k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_t n, Hasher H, uint32_t dig_shift,
             uint32_t dig_mask, uint32_t R, ChunkMap cm, uint32_t nch_host, const Plan* __restrict__ plan,
             const uint32_t* __restrict__ chunk_base, K* __restrict__ out, uint32_t* __restrict__ out_v,
-            uint32_t* err) {
+            uint32_t* err, uint32_t* __restrict__ pos_out) {
     constexpr int IPT = PassCfg<K>::IPT;
     constexpr int TILE = PassCfg<K>::TILE;
     constexpr int G = 16 / sizeof(K);
@@ -481,6 +492,7 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
                 s_keys[pos] = k[j];
                 s_dst[pos] = s_base[d] + r;
                 if (PM) s_pay[pos] = v[j];
+                if (POS) pos_out[t0 + li] = s_base[d] + r;
             }
         }
         __syncthreads();
@@ -823,7 +835,7 @@ cudaError_t launch_down(const K* in, const uint32_t* in_v, uint64_t n, const Has
     if (e != cudaSuccess) return e;
     launch_begin("part_scatter", s);
     kern<<<grid, PASS_THREADS, smem, s>>>(in, in_v, n, H, dig_shift, dig_mask, R, cm, nch_host, plan, base, out, out_v,
-                                          err);
+                                          err, nullptr);
     launch_end("part_scatter", s);
     return cudaGetLastError();
 }
@@ -894,14 +906,14 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     e = cudaMemsetAsync(base, 0, zero_bytes, s);
     // 1. bin histogram + first-pass chunk counts
     if (e == cudaSuccess) {
-        auto kern = k_part_count<K>;
+        auto kern = k_part_count<K, true>;
         const size_t smem = (size_t)P * 4;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) {
             unsigned g = grid_for(kern, PASS_THREADS, smem);
             if (g > nch_a) g = nch_a;
             launch_begin("part_hist", s);
-            kern<<<g, PASS_THREADS, smem, s>>>(keys, n, t.H, P, shift1, R1, nch_a, bin_count, cnt_a);
+            kern<<<g, PASS_THREADS, smem, s>>>(keys, n, t.H, P, shift1, R1, nch_a, bin_count, cnt_a, nullptr);
             launch_end("part_hist", s);
             e = cudaGetLastError();
         }
@@ -917,9 +929,9 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     }
     // 3a. first pass: chunk bases, then the downsweep
     if (e == cudaSuccess) {
-        launch_begin("part_plan", s);
-        k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt_a, pref, cm_a, nch_a, plan, R1, two ? P2 : 1u);
-        launch_end("part_plan", s);
+        launch_begin("chunk_scan", s);
+        k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt_a, pref, cm_a, nch_a, plan, R1, two ? P2 : 1u, nullptr);
+        launch_end("chunk_scan", s);
         e = cudaGetLastError();
     }
     const int pm_first = vals ? 1 : (hv ? 2 : 0);
@@ -939,14 +951,14 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     }
     // 3b. second pass (bins inside each coarse segment)
     if (e == cudaSuccess && two) {
-        launch_begin("part_hist", s);
+        launch_begin("chunk_count", s);
         k_chunk_count<K><<<nch_b_max, PASS_THREADS, 0, s>>>(ka, t.H, cm_b, plan, cnt_b);
-        launch_end("part_hist", s);
+        launch_end("chunk_count", s);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
-            launch_begin("part_plan", s);
-            k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt_b, pref, cm_b, 0u, plan, P2, 1u);
-            launch_end("part_plan", s);
+            launch_begin("chunk_scan", s);
+            k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt_b, pref, cm_b, 0u, plan, P2, 1u, nullptr);
+            launch_end("chunk_scan", s);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
@@ -997,9 +1009,84 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     return e;
 }
 
+// Queries grouped by coarse bucket range: one reduce-then-scan pass with
+// digit = bin >> shift.  pos[i] (optional) = index of query i in q_sorted.
+template <typename K>
+cudaError_t partition_queries_impl(const Table& t, const K* q, uint64_t nq, uint32_t shift, uint32_t C, K* q_sorted,
+                                   uint32_t* pos, cudaStream_t s) {
+    const uint32_t nch = (uint32_t)((nq + CHUNK - 1) / CHUNK);
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_tot = 0;
+    const size_t o_cnt = al((size_t)RADIX * 4);
+    const size_t o_pref = o_cnt + al((size_t)nch * RADIX * 4);
+    const size_t bytes = o_pref + al((size_t)nch * RADIX * 4);
+    void* mem = nullptr;
+    cudaError_t e = dev_alloc(&mem, bytes, s);
+    if (e != cudaSuccess) return e;
+    char* base = static_cast<char*>(mem);
+    uint32_t* digit_total = reinterpret_cast<uint32_t*>(base + o_tot);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(base + o_cnt);
+    uint32_t* pref = reinterpret_cast<uint32_t*>(base + o_pref);
+    e = cudaMemsetAsync(digit_total, 0, (size_t)RADIX * 4, s);
+    if (e == cudaSuccess) {
+        auto kern = k_part_count<K, false>;
+        unsigned g = grid_for(kern, PASS_THREADS, 0);
+        if (g > nch) g = nch;
+        launch_begin("q_part_count", s);
+        kern<<<g, PASS_THREADS, 0, s>>>(q, nq, t.H, 0, shift, C, nch, nullptr, cnt, digit_total);
+        launch_end("q_part_count", s);
+        e = cudaGetLastError();
+    }
+    const ChunkMap cm{false, nq, 0, 0, 1, nullptr, nullptr};
+    if (e == cudaSuccess) {
+        launch_begin("chunk_scan", s);
+        k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt, pref, cm, nch, nullptr, C, 0u, digit_total);
+        launch_end("chunk_scan", s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        auto kern = pos ? k_pass_down<K, 0, true> : k_pass_down<K, 0, false>;
+        const size_t smem = pass_smem_bytes<K>(false);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            launch_begin("q_partition", s);
+            kern<<<nch, PASS_THREADS, smem, s>>>(q, nullptr, nq, t.H, shift, 0xffffffffu, C, cm, nch, nullptr, cnt,
+                                                 q_sorted, nullptr, t.err, pos);
+            launch_end("q_partition", s);
+            e = cudaGetLastError();
+        }
+    }
+    dev_free(mem, s);
+    return e;
+}
+
 }  // namespace
 
 bool partition_supported(uint64_t B) { return (B + BPB - 1) / BPB <= MAX_BINS; }
+
+bool probe_partition_plan(const Table& t, uint64_t q, uint32_t* shift, uint32_t* ncoarse) {
+    const uint64_t P = (t.B + BPB - 1) / BPB;
+    if (P < 2 || P > MAX_BINS || q < (1u << 20)) return false;
+    const uint64_t table_bytes = 4 * (t.B + 1) + (uint64_t)t.key_bytes * t.n;
+    const uint64_t region = 40ull << 20;  // table bytes per coarse range, well inside L2
+    const uint64_t want = (table_bytes + region - 1) / region;
+    if (want < 2) return false;
+    uint32_t sh = 0;
+    while (((P - 1) >> (sh + 1)) + 1 >= want && ((P - 1) >> (sh + 1)) + 1 >= 2) ++sh;
+    while (((P - 1) >> sh) + 1 > RADIX) ++sh;
+    *shift = sh;
+    *ncoarse = (uint32_t)(((P - 1) >> sh) + 1);
+    return true;
+}
+
+cudaError_t partition_queries(const Table& t, const void* d_q, uint64_t q, uint32_t shift, uint32_t ncoarse,
+                              void* q_sorted, uint32_t* pos, cudaStream_t s) {
+    if (t.key_bytes == 4)
+        return partition_queries_impl<uint32_t>(t, static_cast<const uint32_t*>(d_q), q, shift, ncoarse,
+                                                static_cast<uint32_t*>(q_sorted), pos, s);
+    return partition_queries_impl<uint64_t>(t, static_cast<const uint64_t*>(d_q), q, shift, ncoarse,
+                                            static_cast<uint64_t*>(q_sorted), pos, s);
+}
 
 cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values, cudaStream_t s) {
     const uint32_t* vals = static_cast<const uint32_t*>(d_values);

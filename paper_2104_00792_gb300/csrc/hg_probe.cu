@@ -390,21 +390,6 @@ cudaError_t run_probe(const Table& t, const K* qs, uint64_t q, void* counts, uin
     return cudaGetLastError();
 }
 
-template <typename K>
-cudaError_t count_impl(const Table& t, const K* qs, uint64_t q, uint32_t* counts, uint64_t* total, cudaStream_t s) {
-    void* mem = nullptr;
-    LongList L{};
-    const uint32_t cap = (uint32_t)(q < COUNT_LONG_CAP ? q : COUNT_LONG_CAP);
-    cudaError_t e = alloc_list(cap, false, s, &mem, &L);
-    if (e == cudaSuccess) {
-        if (counts && total) e = run_probe<K, OUT_U32, true, false>(t, qs, q, counts, total, L, nullptr, nullptr, s);
-        else if (counts) e = run_probe<K, OUT_U32, false, false>(t, qs, q, counts, nullptr, L, nullptr, nullptr, s);
-        else e = run_probe<K, OUT_NONE, true, false>(t, qs, q, nullptr, total, L, nullptr, nullptr, s);
-    }
-    if (mem) dev_free(mem, s);
-    return e;
-}
-
 // Byte-model helper: stats[0] += sum of walked bucket lengths, stats[1] += the
 // part in buckets longer than WALK_WARP, stats[2] += number of such slots.
 template <typename K>
@@ -430,6 +415,80 @@ k_walk_stats(const K* __restrict__ qs, uint64_t q, const uint32_t* __restrict__ 
         atomicAdd(reinterpret_cast<unsigned long long*>(stats + 1), (unsigned long long)c);
         atomicAdd(reinterpret_cast<unsigned long long*>(stats + 2), (unsigned long long)d);
     }
+}
+
+// counts[i] = counts_sorted[pos[i]]: back from range order to slot order.  The
+// reads follow one forward-moving stream per coarse range, which L2 absorbs.
+__global__ void __launch_bounds__(PROBE_THREADS)
+k_unpermute(const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ pos, uint64_t q, uint32_t* counts) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(counts) | reinterpret_cast<uintptr_t>(pos)) & 15) == 0;
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec) {
+        const uint64_t nv = q / 4;
+        for (uint64_t v = i0; v < nv; v += stride) {
+            const uint4 p4 = ld_stream16(pos + 4 * v);
+            uint4 c;
+            c.x = __ldg(sorted + p4.x);
+            c.y = __ldg(sorted + p4.y);
+            c.z = __ldg(sorted + p4.z);
+            c.w = __ldg(sorted + p4.w);
+            *reinterpret_cast<uint4*>(counts + 4 * v) = c;
+        }
+        for (uint64_t i = nv * 4 + i0; i < q; i += stride) counts[i] = __ldg(sorted + pos[i]);
+    } else {
+        for (uint64_t i = i0; i < q; i += stride) counts[i] = __ldg(sorted + pos[i]);
+    }
+}
+
+template <typename K>
+cudaError_t count_impl(const Table& t, const K* qs, uint64_t q, uint32_t* counts, uint64_t* total, cudaStream_t s) {
+    void* mem = nullptr;
+    LongList L{};
+    const uint32_t cap = (uint32_t)(q < COUNT_LONG_CAP ? q : COUNT_LONG_CAP);
+    cudaError_t e = alloc_list(cap, false, s, &mem, &L);
+    if (e != cudaSuccess) return e;
+
+    // Large query sets against a table larger than L2: group the queries by
+    // coarse bucket range first (the paper's query-side HashGraph, Sec. 3.3,
+    // reduced to the grouping step), so that every range's slice of the table
+    // is probed while it sits in L2; then restore slot order.
+    uint32_t shift = 0, ncoarse = 0;
+    void* pmem = nullptr;
+    if (probe_partition_plan(t, q, &shift, &ncoarse)) {
+        auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+        const size_t o_pos = al(q * sizeof(K));
+        const size_t o_cs = o_pos + (counts ? al(q * 4) : 0);
+        const size_t bytes = o_cs + (counts ? al(q * 4) : 0);
+        e = dev_alloc(&pmem, bytes, s);
+        if (e == cudaSuccess) {
+            char* b = static_cast<char*>(pmem);
+            K* q_sorted = reinterpret_cast<K*>(b);
+            uint32_t* pos = counts ? reinterpret_cast<uint32_t*>(b + o_pos) : nullptr;
+            uint32_t* cs = counts ? reinterpret_cast<uint32_t*>(b + o_cs) : nullptr;
+            e = partition_queries(t, qs, q, shift, ncoarse, q_sorted, pos, s);
+            if (e == cudaSuccess) {
+                if (counts && total) e = run_probe<K, OUT_U32, true, false>(t, q_sorted, q, cs, total, L, nullptr, nullptr, s);
+                else if (counts) e = run_probe<K, OUT_U32, false, false>(t, q_sorted, q, cs, nullptr, L, nullptr, nullptr, s);
+                else e = run_probe<K, OUT_NONE, true, false>(t, q_sorted, q, nullptr, total, L, nullptr, nullptr, s);
+            }
+            if (e == cudaSuccess && counts) {
+                launch_begin("unpermute", s);
+                k_unpermute<<<num_sms() * 8, PROBE_THREADS, 0, s>>>(cs, pos, q, counts);
+                launch_end("unpermute", s);
+                e = cudaGetLastError();
+            }
+            dev_free(pmem, s);
+        }
+        dev_free(mem, s);
+        return e;
+    }
+
+    if (counts && total) e = run_probe<K, OUT_U32, true, false>(t, qs, q, counts, total, L, nullptr, nullptr, s);
+    else if (counts) e = run_probe<K, OUT_U32, false, false>(t, qs, q, counts, nullptr, L, nullptr, nullptr, s);
+    else e = run_probe<K, OUT_NONE, true, false>(t, qs, q, nullptr, total, L, nullptr, nullptr, s);
+    dev_free(mem, s);
+    return e;
 }
 
 }  // namespace

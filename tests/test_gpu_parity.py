@@ -221,3 +221,32 @@ def test_partition_many_hot_buckets_in_one_bin(hg):
     keys = np.repeat(vals, 80)
     rng.shuffle(keys)
     _run_all(hg, keys, 4096, 0, vals[::3].copy(), flags=hg.HG_INDEX_VALUES, check_gather=False)
+
+
+def _probe_only(hg, keys, B, queries, values=None):
+    """Counts, total and join against the oracle (no gather), default build."""
+    ref = oracle.build_table(keys, B, 0, values=values)
+    want = ref.query_count(queries)
+    with hg.hg_build(to_dev(keys), B, 0, values=None if values is None else to_dev(values)) as t:
+        dq = to_dev(queries)
+        counts = torch.empty(queries.size, dtype=torch.int32, device="cuda")
+        total = torch.empty(1, dtype=torch.int64, device="cuda")
+        hg.hg_query_count(t, dq, counts, total)
+        assert np.array_equal(from_dev(counts, np.uint32).astype(np.uint64), want)
+        assert int(from_dev(total, np.uint64)[0]) == int(want.sum())
+        jt = torch.empty(1, dtype=torch.int64, device="cuda")
+        hg.hg_join_count(t, dq, jt)
+        assert int(from_dev(jt, np.uint64)[0]) == int(want.sum())
+        hg.hg_sync(t)
+
+
+def test_grouped_probe_zipf_u32(hg):
+    # table of 48 MB (> the 40 MB range size): queries are grouped by coarse
+    # bucket range before probing, then counts return to slot order
+    wl = W.zipf_large(n=1 << 23, num_buckets=1 << 22, q=(1 << 21) + 3, M=1 << 18, salt=8)
+    _probe_only(hg, wl.keys, 1 << 22, wl.queries)
+
+
+def test_grouped_probe_u64(hg):
+    wl = W.join_kv(n=1 << 22, num_buckets=(1 << 22) - 9, q=(1 << 21) + 1, salt=10)
+    _probe_only(hg, wl.keys, (1 << 22) - 9, wl.queries, values=wl.values)
