@@ -37,7 +37,7 @@ constexpr int BIN_SHIFT = 13;
 constexpr uint32_t BPB = 1u << BIN_SHIFT;   // buckets per bin
 constexpr uint32_t RADIX = 128;             // digits per partition pass
 constexpr uint32_t MAX_BINS = RADIX * RADIX;
-constexpr int PASS_THREADS = 256;
+constexpr int PASS_THREADS = 512;
 constexpr int LOCAL_THREADS = 512;
 constexpr uint32_t CHUNK = 1u << 16;        // keys per reduce-then-scan chunk
 constexpr uint32_t MAX_HOT = 256;           // buckets per bin that may bypass the staging buffer
@@ -49,7 +49,7 @@ constexpr int NTHR = 5;                     // candidate hot-bucket thresholds
 
 template <typename K>
 struct PassCfg {
-    static constexpr int IPT = sizeof(K) == 4 ? 16 : 8;  // elements per thread per tile
+    static constexpr int IPT = sizeof(K) == 4 ? 8 : 4;  // elements per thread per tile
     static constexpr int TILE = PASS_THREADS * IPT;
 };
 
@@ -198,10 +198,10 @@ k_part_count(const K* __restrict__ keys, uint64_t n, Hasher H, uint32_t P, uint3
         for (uint32_t i = threadIdx.x; i < RADIX; i += blockDim.x) s_dig[i] = 0;
         __syncthreads();
         const uint64_t lo = (uint64_t)c * CHUNK, hi = min(n, lo + CHUNK);
-        block_for_range<K, false, 4>(keys, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned m) {
+        block_for_range<K, false, 4>(keys, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned) {
             const uint32_t b = bin_of(k, H);
-            if (BINS) smem_add1(s_hist, b, m);
-            smem_add1(s_dig, b >> dig_shift, m);
+            if (BINS) atomicAdd(s_hist + b, 1u);
+            atomicAdd(s_dig + ((b >> dig_shift) & (RADIX - 1)), 1u);
         });
         __syncthreads();
         for (uint32_t d = threadIdx.x; d < R; d += blockDim.x) {
@@ -228,8 +228,8 @@ k_chunk_count(const K* __restrict__ in, Hasher H, ChunkMap cm, const Plan* __res
     chunk_range(cm, c, seg, first, lo, hi);
     for (uint32_t i = threadIdx.x; i < RADIX; i += blockDim.x) s_dig[i] = 0;
     __syncthreads();
-    block_for_range<K, false, 4>(in, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned m) {
-        smem_add1(s_dig, bin_of(k, H) & (RADIX - 1), m);
+    block_for_range<K, false, 4>(in, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned) {
+        atomicAdd(s_dig + (bin_of(k, H) & (RADIX - 1)), 1u);
     });
     __syncthreads();
     for (uint32_t d = threadIdx.x; d < RADIX; d += blockDim.x) chunk_cnt[(uint64_t)c * RADIX + d] = s_dig[d];
@@ -418,7 +418,7 @@ __device__ __forceinline__ void load_tile(const K* __restrict__ in, const uint32
 }
 
 template <typename K, int PM, bool POS = false>
-__global__ void __launch_bounds__(PASS_THREADS, 3)
+__global__ void __launch_bounds__(PASS_THREADS, 2)
 k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_t n, Hasher H, uint32_t dig_shift,
             uint32_t dig_mask, uint32_t R, ChunkMap cm, uint32_t nch_host, const Plan* __restrict__ plan,
             const uint32_t* __restrict__ chunk_base, K* __restrict__ out, uint32_t* __restrict__ out_v,
@@ -454,17 +454,10 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const uint32_t li = (threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G);
-            const bool ok = li < cnt_tile;
-            const unsigned m = __ballot_sync(FULL_MASK, ok);
-            dr[j] = 0;
-            if (ok) {
-                uint32_t d = (bin_of(k[j], H) >> dig_shift) & dig_mask;
-                if (d >= R) {  // cannot happen for a consistent plan; keep shared memory in bounds
-                    atomicOr(err, DEVERR_BOUNDS);
-                    d = R - 1;
-                }
-                dr[j] = (smem_inc(s_cnt, d, m) << 8) | d;
-            }
+            // the digit is masked to the radix, so shared-memory indices stay in
+            // bounds whatever the key; a consistent plan never needs the mask
+            const uint32_t d = (bin_of(k[j], H) >> dig_shift) & dig_mask & (RADIX - 1);
+            dr[j] = li < cnt_tile ? ((atomicAdd(s_cnt + d, 1u) << 8) | d) : 0xffffffffu;
         }
         __syncthreads();
         // digit offsets inside the tile (first 4 warps), and where each run goes
@@ -482,26 +475,28 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             s_cnt[d] = 0;
         }
         __syncthreads();
+        uint32_t* pos_t = POS ? pos_out + t0 : nullptr;
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
-            const uint32_t li = (threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G);
-            if (li < cnt_tile) {
+            if (dr[j] != 0xffffffffu) {
                 const uint32_t d = dr[j] & 0xffu;
                 const uint32_t r = dr[j] >> 8;
                 const uint32_t pos = s_loc[d] + r;
+                const uint32_t dst = s_base[d] + r;
                 s_keys[pos] = k[j];
-                s_dst[pos] = s_base[d] + r;
+                s_dst[pos] = dst;
                 if (PM) s_pay[pos] = v[j];
-                if (POS) pos_out[t0 + li] = s_base[d] + r;
+                if (POS) pos_t[(threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G)] = dst;
             }
         }
         __syncthreads();
         // prefetch the next tile while this one is written out
         const uint64_t t1 = t0 + TILE;
         if (t1 < hi) load_tile<K, PM>(in, in_v, t1, (uint32_t)min((uint64_t)TILE, hi - t1), vec, k, v);
+        const uint32_t nn = (uint32_t)min(n, (uint64_t)0xffffffffu);
         for (uint32_t i = threadIdx.x; i < cnt_tile; i += PASS_THREADS) {
             const uint32_t dst = s_dst[i];
-            if (dst < n) {
+            if (dst < nn) {
                 out[dst] = s_keys[i];
                 if (PM) out_v[dst] = s_pay[i];
             } else {
