@@ -65,12 +65,40 @@ cudaError_t build_table(Table& t, const void* d_keys, const void* d_values, cuda
 bool partition_supported(uint64_t B);
 cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values, cudaStream_t s);
 
-// Queries grouped by coarse bucket range so that each range's slice of the
-// table is probed while it sits in L2.  probe_partition_plan decides whether
-// it pays off and picks the range width (digit = bin >> shift, ncoarse ranges).
-bool probe_partition_plan(const Table& t, uint64_t q, uint32_t* shift, uint32_t* ncoarse);
-cudaError_t partition_queries(const Table& t, const void* d_q, uint64_t q, uint32_t shift, uint32_t ncoarse,
-                              void* q_sorted, uint32_t* pos, cudaStream_t s);
+// Queries grouped by the table's bins (ranges of 8192 buckets), so that a
+// bin's offsets and keys stay in L1 while its queries are probed; the counts,
+// produced in grouped order, go back to slot order through reverse passes.
+// Chunk c of a partition pass: keys [lo, hi) of segment `seg` (see chunk_range).
+struct ChunkMap {
+    bool segmented;
+    uint64_t n;
+    uint32_t P, P2, nseg;
+    const uint32_t* bin_start;
+    const uint32_t* seg_chunk_start;  // [nseg + 1], segmented only
+};
+struct GroupedQueries {
+    void* mem = nullptr;
+    bool two = false;
+    void* q_grouped = nullptr;  // queries in bin order (padded to a multiple of 4 elements)
+    const uint32_t* bin_start = nullptr;  // [nbins + 1]: bin p's queries are q_grouped[bin_start[p] ..)
+    uint32_t nbins = 0;
+    // reverse-pass records (opaque to callers)
+    ChunkMap cm_a{}, cm_b{};
+    uint32_t nch_a = 0, nch_b_max = 0;
+    const void* plan = nullptr;
+    const uint32_t* dr_a = nullptr;
+    const uint32_t* dr_b = nullptr;
+    const uint2* lb_a = nullptr;
+    const uint2* lb_b = nullptr;
+};
+bool probe_grouping_pays(const Table& t, uint64_t q);
+cudaError_t group_queries(const Table& t, const void* d_q, uint64_t q, GroupedQueries* g, cudaStream_t s);
+cudaError_t ungroup_counts(const Table& t, const GroupedQueries* g, const uint32_t* cs, uint32_t* tmp,
+                           uint32_t* counts, cudaStream_t s);
+void group_release(GroupedQueries* g, cudaStream_t s);
+
+// Buckets per bin of the partitioned build and of the query grouping.
+constexpr uint32_t BIN_BUCKETS = 8192;
 
 // Probe entry points.  Return a CUDA error.
 //   counts: u32 per slot (may be null); total: u64 sum (may be null).

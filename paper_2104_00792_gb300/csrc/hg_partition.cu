@@ -40,6 +40,7 @@ constexpr uint32_t MAX_BINS = RADIX * RADIX;
 constexpr int PASS_THREADS = 512;
 constexpr int LOCAL_THREADS = 512;
 constexpr uint32_t CHUNK = 1u << 16;        // keys per reduce-then-scan chunk
+constexpr uint32_t TILES_PER_CHUNK = CHUNK / 2048;  // upper bound for either key width
 constexpr uint32_t MAX_HOT = 256;           // buckets per bin that may bypass the staging buffer
 constexpr size_t LOCAL_STAGE_BYTES = 72 * 1024;
 constexpr uint32_t HUGE_T = 1u << 18;       // bins with more keys are split over many CTAs
@@ -151,14 +152,7 @@ struct Plan {
 
 // Chunk c of a pass: keys [lo, hi) of segment `seg`.  Single-segment passes
 // cut [0, n) into CHUNK-key pieces; segmented passes cut each segment
-// [bin_start[s * P2], bin_start[(s + 1) * P2]) separately.
-struct ChunkMap {
-    bool segmented;
-    uint64_t n;
-    uint32_t P, P2, nseg;
-    const uint32_t* bin_start;
-    const uint32_t* seg_chunk_start;  // [nseg + 1], segmented only
-};
+// [bin_start[s * P2], bin_start[(s + 1) * P2]) separately (ChunkMap).
 
 __device__ __forceinline__ void chunk_range(const ChunkMap& cm, uint32_t c, uint32_t& seg, uint32_t& first,
                                             uint64_t& lo, uint64_t& hi) {
@@ -278,7 +272,7 @@ k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uin
     }
     if (threadIdx.x == 0) {
         bin_start[P] = running;
-        offsets[B] = (uint32_t)n;
+        if (offsets) offsets[B] = (uint32_t)n;
     }
     __syncthreads();
     // second-pass chunks per coarse segment
@@ -417,20 +411,26 @@ __device__ __forceinline__ void load_tile(const K* __restrict__ in, const uint32
     }
 }
 
-template <typename K, int PM, bool POS = false>
+// DR: also record, for the reverse pass, each input element's (rank << 8 |
+// digit) in dr_out (input order) and each tile's (loc, base) per digit in
+// tile_lb[c * TILES_PER_CHUNK + tile][RADIX].
+template <typename K, int PM, bool DR = false>
 __global__ void __launch_bounds__(PASS_THREADS, 2)
 k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_t n, Hasher H, uint32_t dig_shift,
             uint32_t dig_mask, uint32_t R, ChunkMap cm, uint32_t nch_host, const Plan* __restrict__ plan,
             const uint32_t* __restrict__ chunk_base, K* __restrict__ out, uint32_t* __restrict__ out_v,
-            uint32_t* err, uint32_t* __restrict__ pos_out) {
+            uint32_t* err, uint32_t* __restrict__ dr_out, uint2* __restrict__ tile_lb) {
     constexpr int IPT = PassCfg<K>::IPT;
     constexpr int TILE = PassCfg<K>::TILE;
     constexpr int G = 16 / sizeof(K);
+    constexpr bool PACK = sizeof(K) == 4;  // (key, destination) staged as one 8-byte word
     extern __shared__ __align__(16) unsigned char smem[];
-    K* s_keys = reinterpret_cast<K*>(smem);
+    uint2* s_kd = reinterpret_cast<uint2*>(smem);                       // PACK: key, destination
+    K* s_keys = reinterpret_cast<K*>(smem);                             // !PACK
     uint32_t* s_dst = reinterpret_cast<uint32_t*>(smem + TILE * sizeof(K));
-    uint32_t* s_pay = s_dst + TILE;
-    __shared__ uint32_t s_cnt[RADIX], s_loc[RADIX], s_base[RADIX], s_run[RADIX], s_warp[4];
+    uint32_t* s_pay = reinterpret_cast<uint32_t*>(smem + (size_t)TILE * 8 + (PACK ? 0 : (size_t)TILE * 4));
+    __shared__ uint32_t s_cnt[RADIX], s_run[RADIX], s_warp[4];
+    __shared__ uint2 s_lb[RADIX];  // (offset of the digit's run inside the tile, its destination)
 
     const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
     const uint32_t c = blockIdx.x;
@@ -448,6 +448,7 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
     K k[IPT];
     uint32_t v[IPT];
     if (lo < hi) load_tile<K, PM>(in, in_v, lo, (uint32_t)min((uint64_t)TILE, hi - lo), vec, k, v);
+    const uint32_t nn = (uint32_t)min(n, (uint64_t)0xffffffffu);
     for (uint64_t t0 = lo; t0 < hi; t0 += TILE) {
         const uint32_t cnt_tile = (uint32_t)min((uint64_t)TILE, hi - t0);
         uint32_t dr[IPT];  // rank << 8 | digit
@@ -469,38 +470,107 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             asm volatile("bar.sync 1, 128;");
             uint32_t wp = 0;
             for (uint32_t w = 0; w < (d >> 5); ++w) wp += s_warp[w];
-            s_loc[d] = wp + incl - cd;
-            s_base[d] = s_run[d];
+            s_lb[d] = make_uint2(wp + incl - cd, s_run[d]);
+            if (DR) tile_lb[((uint64_t)c * TILES_PER_CHUNK + (t0 - lo) / TILE) * RADIX + d] = s_lb[d];
             s_run[d] += cd;
             s_cnt[d] = 0;
         }
         __syncthreads();
-        uint32_t* pos_t = POS ? pos_out + t0 : nullptr;
+        uint32_t* dr_t = DR ? dr_out + t0 : nullptr;
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             if (dr[j] != 0xffffffffu) {
-                const uint32_t d = dr[j] & 0xffu;
                 const uint32_t r = dr[j] >> 8;
-                const uint32_t pos = s_loc[d] + r;
-                const uint32_t dst = s_base[d] + r;
-                s_keys[pos] = k[j];
-                s_dst[pos] = dst;
+                const uint2 lb = s_lb[dr[j] & 0xffu];
+                const uint32_t pos = lb.x + r;
+                const uint32_t dst = lb.y + r;
+                if (PACK) {
+                    s_kd[pos] = make_uint2((uint32_t)k[j], dst);
+                } else {
+                    s_keys[pos] = k[j];
+                    s_dst[pos] = dst;
+                }
                 if (PM) s_pay[pos] = v[j];
-                if (POS) pos_t[(threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G)] = dst;
+                if (DR) dr_t[(threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G)] = dr[j];
             }
         }
         __syncthreads();
         // prefetch the next tile while this one is written out
         const uint64_t t1 = t0 + TILE;
         if (t1 < hi) load_tile<K, PM>(in, in_v, t1, (uint32_t)min((uint64_t)TILE, hi - t1), vec, k, v);
-        const uint32_t nn = (uint32_t)min(n, (uint64_t)0xffffffffu);
         for (uint32_t i = threadIdx.x; i < cnt_tile; i += PASS_THREADS) {
-            const uint32_t dst = s_dst[i];
+            K key;
+            uint32_t dst;
+            if (PACK) {
+                const uint2 kd = s_kd[i];
+                key = (K)kd.x;
+                dst = kd.y;
+            } else {
+                key = s_keys[i];
+                dst = s_dst[i];
+            }
             if (dst < nn) {
-                out[dst] = s_keys[i];
+                out[dst] = key;
                 if (PM) out_v[dst] = s_pay[i];
             } else {
                 atomicOr(err, DEVERR_BOUNDS);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- reverse --
+// Undo one DR-recording pass for 32-bit values: src is in the pass's output
+// order, dst receives the values in its input order.  Each tile reads the runs
+// it wrote (contiguous, so the reads coalesce) into shared memory in its
+// staging order, then every element takes its value from its recorded
+// (rank, digit) and writes it in input order.
+template <typename K>
+__global__ void __launch_bounds__(PASS_THREADS, 2)
+k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, ChunkMap cm, uint32_t nch_host,
+               const Plan* __restrict__ plan, const uint32_t* __restrict__ dr_in, const uint2* __restrict__ tile_lb,
+               uint32_t* err) {
+    constexpr int TILE = PassCfg<K>::TILE;
+    __shared__ uint32_t s_val[TILE];
+    __shared__ uint8_t s_dig[TILE];
+    __shared__ uint2 s_lb[RADIX];
+    const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
+    const uint32_t c = blockIdx.x;
+    if (c >= nch) return;
+    uint32_t seg, first;
+    uint64_t lo, hi;
+    chunk_range(cm, c, seg, first, lo, hi);
+    for (uint64_t t0 = lo; t0 < hi; t0 += TILE) {
+        const uint32_t cnt_tile = (uint32_t)min((uint64_t)TILE, hi - t0);
+        if (threadIdx.x < RADIX)
+            s_lb[threadIdx.x] = tile_lb[((uint64_t)c * TILES_PER_CHUNK + (t0 - lo) / TILE) * RADIX + threadIdx.x];
+        __syncthreads();
+        // every element marks its staging position with its digit ...
+        uint32_t drs[TILE / PASS_THREADS];
+#pragma unroll
+        for (int j = 0; j < TILE / PASS_THREADS; ++j) {
+            const uint32_t li = threadIdx.x + j * PASS_THREADS;
+            drs[j] = li < cnt_tile ? dr_in[t0 + li] : 0xffffffffu;
+            if (drs[j] != 0xffffffffu) {
+                const uint32_t p = s_lb[drs[j] & 0xffu].x + (drs[j] >> 8);
+                if (p < (uint32_t)TILE) s_dig[p] = (uint8_t)(drs[j] & 0xffu);
+                else atomicOr(err, DEVERR_BOUNDS);
+            }
+        }
+        __syncthreads();
+        // ... so that the tile's runs are read back contiguously in staging order
+        for (uint32_t i = threadIdx.x; i < cnt_tile; i += PASS_THREADS) {
+            const uint2 lb = s_lb[s_dig[i]];
+            s_val[i] = src[lb.y + (i - lb.x)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < TILE / PASS_THREADS; ++j) {
+            const uint32_t li = threadIdx.x + j * PASS_THREADS;
+            if (drs[j] != 0xffffffffu) {
+                const uint32_t p = s_lb[drs[j] & 0xffu].x + (drs[j] >> 8);
+                if (p < (uint32_t)TILE) dst[t0 + li] = s_val[p];
             }
         }
         __syncthreads();
@@ -808,7 +878,8 @@ size_t local_smem_bytes(size_t key_bytes, bool hv) {
 template <typename K>
 size_t pass_smem_bytes(bool payload) {
     constexpr int TILE = PassCfg<K>::TILE;
-    return (size_t)TILE * sizeof(K) + (size_t)TILE * 4 + (payload ? (size_t)TILE * 4 : 0);
+    // u32 keys: (key, destination) pairs; u64 keys: keys then destinations
+    return (size_t)TILE * 8 + (sizeof(K) == 4 ? 0 : (size_t)TILE * 4) + (payload ? (size_t)TILE * 4 : 0);
 }
 
 template <typename Kern>
@@ -830,7 +901,7 @@ cudaError_t launch_down(const K* in, const uint32_t* in_v, uint64_t n, const Has
     if (e != cudaSuccess) return e;
     launch_begin("part_scatter", s);
     kern<<<grid, PASS_THREADS, smem, s>>>(in, in_v, n, H, dig_shift, dig_mask, R, cm, nch_host, plan, base, out, out_v,
-                                          err, nullptr);
+                                          err, nullptr, nullptr);
     launch_end("part_scatter", s);
     return cudaGetLastError();
 }
@@ -1004,89 +1075,181 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     return e;
 }
 
-// Queries grouped by coarse bucket range: one reduce-then-scan pass with
-// digit = bin >> shift.  pos[i] (optional) = index of query i in q_sorted.
+// Queries grouped by the table's bins (bin = bucket >> BIN_SHIFT) with the
+// build's one- or two-pass partition, recording what the reverse passes need.
 template <typename K>
-cudaError_t partition_queries_impl(const Table& t, const K* q, uint64_t nq, uint32_t shift, uint32_t C, K* q_sorted,
-                                   uint32_t* pos, cudaStream_t s) {
-    const uint32_t nch = (uint32_t)((nq + CHUNK - 1) / CHUNK);
+cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQueries* g, cudaStream_t s) {
+    const uint64_t B = t.B;
+    const uint32_t P = (uint32_t)((B + BPB - 1) / BPB);
+    const uint32_t P2 = P <= RADIX ? P : RADIX;
+    const uint32_t P1 = (P + P2 - 1) / P2;
+    const bool two = P1 > 1;
+    const uint32_t nch_a = (uint32_t)((nq + CHUNK - 1) / CHUNK);
+    const uint32_t nch_b_max = nch_a + P1 + 1;
+    const uint32_t shift1 = two ? 7u : 0u;
+    const uint32_t R1 = two ? P1 : P;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t o_tot = 0;
-    const size_t o_cnt = al((size_t)RADIX * 4);
-    const size_t o_pref = o_cnt + al((size_t)nch * RADIX * 4);
-    const size_t bytes = o_pref + al((size_t)nch * RADIX * 4);
-    void* mem = nullptr;
-    cudaError_t e = dev_alloc(&mem, bytes, s);
+    size_t off = 0;
+    const size_t o_cnt = off; off += al((size_t)P * 4);
+    const size_t o_ctr = off; off += al(64);
+    const size_t zero_bytes = off;
+    const size_t o_ca = off; off += al((size_t)nch_a * RADIX * 4);
+    const size_t o_cb = off; off += al(two ? (size_t)nch_b_max * RADIX * 4 : 0);
+    const size_t o_pref = off; off += al((size_t)nch_b_max * RADIX * 4);
+    const size_t o_start = off; off += al((size_t)(P + 1) * 4);
+    const size_t o_work = off; off += al((size_t)P * 4);
+    const size_t o_seg = off; off += al((size_t)(P1 + 1) * 4);
+    const size_t o_hbin = off; off += al((size_t)MAX_HUGE * 4);
+    const size_t o_hcs = off; off += al((size_t)(MAX_HUGE + 1) * 4);
+    const size_t o_plan = off; off += al(sizeof(Plan));
+    const size_t o_lba = off; off += al((size_t)nch_a * TILES_PER_CHUNK * RADIX * 8);
+    const size_t o_lbb = off; off += al(two ? (size_t)nch_b_max * TILES_PER_CHUNK * RADIX * 8 : 0);
+    const size_t o_dra = off; off += al(nq * 4);
+    const size_t o_drb = off; off += al(two ? nq * 4 : 0);
+    const size_t o_qa = off; off += al(two ? nq * sizeof(K) : 0);
+    const size_t o_qb = off; off += al((nq + 4) * sizeof(K));
+    cudaError_t e = dev_alloc(&g->mem, off, s);
     if (e != cudaSuccess) return e;
-    char* base = static_cast<char*>(mem);
-    uint32_t* digit_total = reinterpret_cast<uint32_t*>(base + o_tot);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(base + o_cnt);
+    char* base = static_cast<char*>(g->mem);
+    uint32_t* bin_count = reinterpret_cast<uint32_t*>(base + o_cnt);
+    uint32_t* cnt_a = reinterpret_cast<uint32_t*>(base + o_ca);
+    uint32_t* cnt_b = reinterpret_cast<uint32_t*>(base + o_cb);
     uint32_t* pref = reinterpret_cast<uint32_t*>(base + o_pref);
-    e = cudaMemsetAsync(digit_total, 0, (size_t)RADIX * 4, s);
+    uint32_t* bin_start = reinterpret_cast<uint32_t*>(base + o_start);
+    uint32_t* seg = reinterpret_cast<uint32_t*>(base + o_seg);
+    Plan* plan = reinterpret_cast<Plan*>(base + o_plan);
+    uint2* lb_a = reinterpret_cast<uint2*>(base + o_lba);
+    uint2* lb_b = reinterpret_cast<uint2*>(base + o_lbb);
+    uint32_t* dr_a = reinterpret_cast<uint32_t*>(base + o_dra);
+    uint32_t* dr_b = reinterpret_cast<uint32_t*>(base + o_drb);
+    K* qa = reinterpret_cast<K*>(base + o_qa);
+    K* qb = reinterpret_cast<K*>(base + o_qb);
+    const ChunkMap cm_a{false, nq, P, P2, 1u, bin_start, nullptr};
+    const ChunkMap cm_b{true, nq, P, P2, P1, bin_start, seg};
+    g->two = two;
+
+    e = cudaMemsetAsync(base, 0, zero_bytes, s);
     if (e == cudaSuccess) {
-        auto kern = k_part_count<K, false>;
-        unsigned g = grid_for(kern, PASS_THREADS, 0);
-        if (g > nch) g = nch;
-        launch_begin("q_part_count", s);
-        kern<<<g, PASS_THREADS, 0, s>>>(q, nq, t.H, 0, shift, C, nch, nullptr, cnt, digit_total);
-        launch_end("q_part_count", s);
-        e = cudaGetLastError();
-    }
-    const ChunkMap cm{false, nq, 0, 0, 1, nullptr, nullptr};
-    if (e == cudaSuccess) {
-        launch_begin("chunk_scan", s);
-        k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt, pref, cm, nch, nullptr, C, 0u, digit_total);
-        launch_end("chunk_scan", s);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        auto kern = pos ? k_pass_down<K, 0, true> : k_pass_down<K, 0, false>;
-        const size_t smem = pass_smem_bytes<K>(false);
+        auto kern = k_part_count<K, true>;
+        const size_t smem = (size_t)P * 4;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) {
-            launch_begin("q_partition", s);
-            kern<<<nch, PASS_THREADS, smem, s>>>(q, nullptr, nq, t.H, shift, 0xffffffffu, C, cm, nch, nullptr, cnt,
-                                                 q_sorted, nullptr, t.err, pos);
-            launch_end("q_partition", s);
+            unsigned gr = grid_for(kern, PASS_THREADS, smem);
+            if (gr > nch_a) gr = nch_a;
+            launch_begin("q_part_count", s);
+            kern<<<gr, PASS_THREADS, smem, s>>>(q, nq, t.H, P, shift1, R1, nch_a, bin_count, cnt_a, nullptr);
+            launch_end("q_part_count", s);
             e = cudaGetLastError();
         }
     }
-    dev_free(mem, s);
+    if (e == cudaSuccess) {
+        launch_begin("part_plan", s);
+        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, nq, 0xffffffffu, bin_start, seg,
+                                       reinterpret_cast<uint32_t*>(base + o_work),
+                                       reinterpret_cast<uint32_t*>(base + o_hbin),
+                                       reinterpret_cast<uint32_t*>(base + o_hcs), plan, nullptr, B);
+        launch_end("part_plan", s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        launch_begin("chunk_scan", s);
+        k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt_a, pref, cm_a, nch_a, plan, R1, two ? P2 : 1u, nullptr);
+        launch_end("chunk_scan", s);
+        e = cudaGetLastError();
+    }
+    auto down = [&](const K* in, K* out, const ChunkMap& cm, uint32_t nch_host, uint32_t grid, uint32_t sh,
+                    uint32_t mask, uint32_t R, const uint32_t* cbase, uint32_t* dr, uint2* lb) {
+        auto kern = k_pass_down<K, 0, true>;
+        const size_t smem = pass_smem_bytes<K>(false);
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r != cudaSuccess) return r;
+        launch_begin("q_partition", s);
+        kern<<<grid, PASS_THREADS, smem, s>>>(in, nullptr, nq, t.H, sh, mask, R, cm, nch_host, plan, cbase, out,
+                                              nullptr, t.err, dr, lb);
+        launch_end("q_partition", s);
+        return cudaGetLastError();
+    };
+    if (e == cudaSuccess) e = down(q, two ? qa : qb, cm_a, nch_a, nch_a, shift1, RADIX - 1, R1, cnt_a, dr_a, lb_a);
+    if (e == cudaSuccess && two) {
+        launch_begin("chunk_count", s);
+        k_chunk_count<K><<<nch_b_max, PASS_THREADS, 0, s>>>(qa, t.H, cm_b, plan, cnt_b);
+        launch_end("chunk_count", s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            launch_begin("chunk_scan", s);
+            k_chunk_scan<<<RADIX, 1024, 0, s>>>(cnt_b, pref, cm_b, 0u, plan, P2, 1u, nullptr);
+            launch_end("chunk_scan", s);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = down(qa, qb, cm_b, 0u, nch_b_max, 0, RADIX - 1, P2, cnt_b, dr_b, lb_b);
+    }
+    g->q_grouped = qb;
+    g->bin_start = bin_start;
+    g->nbins = P;
+    // what the reverse passes need
+    g->cm_a = cm_a;
+    g->cm_b = cm_b;
+    g->nch_a = nch_a;
+    g->nch_b_max = nch_b_max;
+    g->plan = plan;
+    g->dr_a = dr_a;
+    g->dr_b = dr_b;
+    g->lb_a = lb_a;
+    g->lb_b = lb_b;
     return e;
+}
+
+template <typename K>
+cudaError_t ungroup_counts_impl(const Table& t, const GroupedQueries* g, const uint32_t* cs, uint32_t* tmp,
+                                uint32_t* counts, cudaStream_t s) {
+    const Plan* plan = static_cast<const Plan*>(g->plan);
+    if (g->two) {
+        launch_begin("q_reverse", s);
+        k_pass_reverse<K><<<g->nch_b_max, PASS_THREADS, 0, s>>>(cs, tmp, g->cm_b, 0u, plan, g->dr_b, g->lb_b,
+                                                               t.err);
+        launch_end("q_reverse", s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        cs = tmp;
+    }
+    launch_begin("q_reverse", s);
+    k_pass_reverse<K><<<g->nch_a, PASS_THREADS, 0, s>>>(cs, counts, g->cm_a, g->nch_a, plan, g->dr_a, g->lb_a,
+                                                       t.err);
+    launch_end("q_reverse", s);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 bool partition_supported(uint64_t B) { return (B + BPB - 1) / BPB <= MAX_BINS; }
 
-bool probe_partition_plan(const Table& t, uint64_t q, uint32_t* shift, uint32_t* ncoarse) {
-    const uint64_t P = (t.B + BPB - 1) / BPB;
-    if (P < 2 || P > MAX_BINS || q < (1u << 20)) return false;
-    const uint64_t table_bytes = 4 * (t.B + 1) + (uint64_t)t.key_bytes * t.n;
-    const uint64_t region = 40ull << 20;  // table bytes per coarse range, well inside L2
-    const uint64_t want = (table_bytes + region - 1) / region;
-    if (want < 2) return false;
-    uint32_t sh = 0;
-    while (((P - 1) >> (sh + 1)) + 1 >= want && ((P - 1) >> (sh + 1)) + 1 >= 2) ++sh;
-    while (((P - 1) >> sh) + 1 > RADIX) ++sh;
-    *shift = sh;
-    *ncoarse = (uint32_t)(((P - 1) >> sh) + 1);
-    return true;
-}
-
-cudaError_t partition_queries(const Table& t, const void* d_q, uint64_t q, uint32_t shift, uint32_t ncoarse,
-                              void* q_sorted, uint32_t* pos, cudaStream_t s) {
-    if (t.key_bytes == 4)
-        return partition_queries_impl<uint32_t>(t, static_cast<const uint32_t*>(d_q), q, shift, ncoarse,
-                                                static_cast<uint32_t*>(q_sorted), pos, s);
-    return partition_queries_impl<uint64_t>(t, static_cast<const uint64_t*>(d_q), q, shift, ncoarse,
-                                            static_cast<uint64_t*>(q_sorted), pos, s);
-}
-
 cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values, cudaStream_t s) {
     const uint32_t* vals = static_cast<const uint32_t*>(d_values);
     if (t.key_bytes == 4) return build_partitioned_impl<uint32_t>(t, static_cast<const uint32_t*>(d_keys), vals, s);
     return build_partitioned_impl<uint64_t>(t, static_cast<const uint64_t*>(d_keys), vals, s);
+}
+
+bool probe_grouping_pays(const Table& t, uint64_t q) {
+    const uint64_t P = (t.B + BPB - 1) / BPB;
+    if (P < 2 || P > MAX_BINS || q < (1u << 20)) return false;
+    const uint64_t table_bytes = 4 * (t.B + 1) + (uint64_t)t.key_bytes * t.n;
+    return table_bytes > (48ull << 20);  // the table does not stay in L2
+}
+
+cudaError_t group_queries(const Table& t, const void* d_q, uint64_t q, GroupedQueries* g, cudaStream_t s) {
+    if (t.key_bytes == 4) return group_queries_impl<uint32_t>(t, static_cast<const uint32_t*>(d_q), q, g, s);
+    return group_queries_impl<uint64_t>(t, static_cast<const uint64_t*>(d_q), q, g, s);
+}
+
+cudaError_t ungroup_counts(const Table& t, const GroupedQueries* g, const uint32_t* cs, uint32_t* tmp,
+                           uint32_t* counts, cudaStream_t s) {
+    if (t.key_bytes == 4) return ungroup_counts_impl<uint32_t>(t, g, cs, tmp, counts, s);
+    return ungroup_counts_impl<uint64_t>(t, g, cs, tmp, counts, s);
+}
+
+void group_release(GroupedQueries* g, cudaStream_t s) {
+    if (g->mem) dev_free(g->mem, s);
+    g->mem = nullptr;
 }
 
 }  // namespace hg

@@ -417,28 +417,203 @@ k_walk_stats(const K* __restrict__ qs, uint64_t q, const uint32_t* __restrict__ 
     }
 }
 
-// counts[i] = counts_sorted[pos[i]]: back from range order to slot order.  The
-// reads follow one forward-moving stream per coarse range, which L2 absorbs.
+// Probe over queries grouped by table bin: each CTA takes RANGE consecutive
+// grouped queries at a time, so the bins it touches (their offsets and keys,
+// about 100 KB) stay in L1 while their queries are answered.  Same per-slot
+// work as k_probe; q_grouped is padded to a multiple of 16 bytes.
+constexpr uint32_t RANGE = 8192;
+
+template <typename K, int OUT, bool TOTAL>
 __global__ void __launch_bounds__(PROBE_THREADS)
-k_unpermute(const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ pos, uint64_t q, uint32_t* counts) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const bool vec = ((reinterpret_cast<uintptr_t>(counts) | reinterpret_cast<uintptr_t>(pos)) & 15) == 0;
-    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (vec) {
-        const uint64_t nv = q / 4;
-        for (uint64_t v = i0; v < nv; v += stride) {
-            const uint4 p4 = ld_stream16(pos + 4 * v);
-            uint4 c;
-            c.x = __ldg(sorted + p4.x);
-            c.y = __ldg(sorted + p4.y);
-            c.z = __ldg(sorted + p4.z);
-            c.w = __ldg(sorted + p4.w);
-            *reinterpret_cast<uint4*>(counts + 4 * v) = c;
+k_probe_ranges(const K* __restrict__ qs, uint64_t q, const K* __restrict__ keys, const uint32_t* __restrict__ offs,
+               Hasher H, uint32_t n_keys, void* counts, uint64_t* total, LongList L) {
+    constexpr int VEC = KeyVec<K>::N;
+    const unsigned lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint64_t nranges = (q + RANGE - 1) / RANGE;
+    uint64_t acc = 0;
+    uint64_t slot[VEC];
+    bool valid[VEC];
+    K qk[VEC];
+    for (uint64_t r = blockIdx.x; r < nranges; r += gridDim.x) {
+        const uint64_t r0 = r * RANGE;
+        const uint64_t g_end = (min(q, r0 + RANGE) - r0 + VEC - 1) / VEC;  // vector groups in the range
+        for (uint64_t g0 = (uint64_t)warp * 32; g0 < g_end; g0 += (uint64_t)nwarps * 32) {
+            const uint64_t g = g0 + lane;
+            const bool ok = g < g_end;
+            KeyVec<K> kv;
+            if (ok) kv = load_keys16(qs + r0 + g * VEC);
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                slot[j] = r0 + g * VEC + j;
+                valid[j] = ok && slot[j] < q;
+                qk[j] = valid[j] ? kv.k[j] : (K)0;
+            }
+            probe_group<K, OUT, false>(slot, valid, qk, keys, nullptr, offs, H, n_keys, counts, L, nullptr, nullptr,
+                                       acc);
         }
-        for (uint64_t i = nv * 4 + i0; i < q; i += stride) counts[i] = __ldg(sorted + pos[i]);
-    } else {
-        for (uint64_t i = i0; i < q; i += stride) counts[i] = __ldg(sorted + pos[i]);
     }
+    if (TOTAL) {
+        const uint64_t sum = block_sum(acc);
+        if (threadIdx.x == 0 && sum) atomicAdd(reinterpret_cast<unsigned long long*>(total), (unsigned long long)sum);
+    }
+}
+
+// One table bin per CTA work item (the paper's per-bucket intersection,
+// Sec. 3.3, done a bin of 8192 buckets at a time): the bin's offsets and, when
+// they fit, its keys are copied into shared memory with coalesced loads, then
+// the bin's grouped queries are answered from shared memory.  Buckets longer
+// than WALK_WARP keys go to the long-bucket list as in the direct probe.
+constexpr uint32_t BIN_KEY_BYTES = 64 * 1024;
+constexpr int BIN_PROBE_THREADS = 512;
+
+template <typename K, int OUT, bool TOTAL>
+__global__ void __launch_bounds__(BIN_PROBE_THREADS, 2)
+k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, uint32_t nbins,
+             const K* __restrict__ keys, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
+             uint64_t* total, LongList L, uint32_t* work_ctr) {
+    constexpr uint32_t KCAP = BIN_KEY_BYTES / sizeof(K);
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(smem);                       // BIN_BUCKETS + 1
+    K* s_keys = reinterpret_cast<K*>(smem + ((BIN_BUCKETS + 1) * 4 + 15) / 16 * 16);
+    __shared__ uint32_t s_item;
+    const unsigned lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint64_t B = H.B;
+    uint64_t acc = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work_ctr, 1u);
+        __syncthreads();
+        const uint32_t p = s_item;
+        if (p >= nbins) break;
+        const uint32_t q0 = qbin_start[p], q1 = qbin_start[p + 1];
+        if (q0 == q1) {
+            __syncthreads();
+            continue;
+        }
+        const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
+        const uint32_t nb = (uint32_t)min((uint64_t)BIN_BUCKETS, B - b0);
+        for (uint32_t j = threadIdx.x; j <= nb; j += blockDim.x) s_off[j] = min(__ldg(offs + b0 + j), n_keys);
+        __syncthreads();
+        const uint32_t k0 = s_off[0], k1 = max(k0, s_off[nb]);
+        const bool staged = k1 - k0 <= KCAP;
+        if (staged)
+            for (uint32_t i = threadIdx.x; i < k1 - k0; i += blockDim.x) s_keys[i] = __ldg(keys + k0 + i);
+        __syncthreads();
+        const K* kb = staged ? s_keys : keys + k0;  // keys of the bin, indexed from k0
+        for (uint32_t i0 = q0 + warp * 32; i0 < q1; i0 += nwarps * 32) {
+            const uint32_t i = i0 + lane;
+            const bool ok = i < q1;
+            const K key = ok ? qs[i] : (K)0;
+            uint32_t lo = 0, hi = 0;
+            if (ok) {
+                uint32_t j = bucket_of(key, H) - (uint32_t)b0;
+                if (j >= nb) j = nb - 1;  // queries of this bin hash into it by construction
+                lo = s_off[j] - k0;
+                hi = max(s_off[j + 1], s_off[j]) - k0;
+            }
+            const uint32_t len = hi - lo;
+            uint8_t cls = !ok ? CLS_NONE : len <= WALK_LANE ? CLS_LANE : len <= WALK_WARP ? CLS_WARP : CLS_LONG;
+            uint32_t cnt = 0;
+            if (cls == CLS_LANE)
+                for (uint32_t x = lo; x < hi; ++x) cnt += (kb[x] == key);
+            // long buckets to the list (warp-aggregated); on overflow the warp walks them
+            const unsigned lm = __ballot_sync(FULL_MASK, cls == CLS_LONG);
+            if (lm) {
+                const int leader = __ffs(lm) - 1;
+                uint32_t base = 0;
+                if ((int)lane == leader) base = atomicAdd(L.n, (uint32_t)__popc(lm));
+                base = __shfl_sync(FULL_MASK, base, leader);
+                if (cls == CLS_LONG) {
+                    const uint32_t pos = base + __popc(lm & lanemask_lt());
+                    if (pos < L.cap) L.slot[pos] = i;
+                    else cls = CLS_WARP;
+                }
+            }
+            unsigned mm = __ballot_sync(FULL_MASK, cls == CLS_WARP);
+            while (mm) {
+                const int src = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const uint32_t l = __shfl_sync(FULL_MASK, lo, src);
+                const uint32_t h = __shfl_sync(FULL_MASK, hi, src);
+                const K kk = __shfl_sync(FULL_MASK, key, src);
+                uint32_t c = 0;
+                for (uint32_t x = l + lane; x < h; x += 32) c += (kb[x] == kk);
+                c = __reduce_add_sync(FULL_MASK, c);
+                if ((int)lane == src) cnt = c;
+            }
+            if (ok) {
+                if (OUT == OUT_U32) static_cast<uint32_t*>(counts)[i] = cnt;
+                if (OUT == OUT_U64) static_cast<uint64_t*>(counts)[i] = cnt;
+                acc += cnt;
+            }
+        }
+        __syncthreads();
+    }
+    if (TOTAL) {
+        const uint64_t sum = block_sum(acc);
+        if (threadIdx.x == 0 && sum) atomicAdd(reinterpret_cast<unsigned long long*>(total), (unsigned long long)sum);
+    }
+}
+
+template <typename K, int OUT, bool TOTAL>
+cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts, uint64_t* total,
+                           const LongList& L, uint32_t* work_ctr, cudaStream_t s) {
+    const K* keys = static_cast<const K*>(t.keys);
+    const K* qs = static_cast<const K*>(g.q_grouped);
+    {
+        auto kern = k_probe_bins<K, OUT, TOTAL>;
+        const size_t smem = ((BIN_BUCKETS + 1) * 4 + 15) / 16 * 16 + BIN_KEY_BYTES;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BIN_PROBE_THREADS, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        launch_begin("probe", s);
+        kern<<<num_sms() * per_sm, BIN_PROBE_THREADS, smem, s>>>(qs, g.bin_start, g.nbins, keys, t.offsets, t.H,
+                                                                 (uint32_t)t.n, counts, total, L, work_ctr);
+        launch_end("probe", s);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    launch_begin("long_prep", s);
+    k_long_prep<K><<<1, 1024, 0, s>>>(qs, t.offsets, t.H, (uint32_t)t.n, L);
+    launch_end("long_prep", s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto kern = k_long<K, OUT, TOTAL, false>;
+    launch_begin("long", s);
+    kern<<<persistent_grid(kern), PROBE_THREADS, 0, s>>>(qs, keys, t.values, t.offsets, t.H, (uint32_t)t.n, L, counts,
+                                                       total, nullptr, nullptr);
+    launch_end("long", s);
+    return cudaGetLastError();
+}
+
+template <typename K, int OUT, bool TOTAL>
+cudaError_t run_probe_ranges(const Table& t, const K* qs, uint64_t q, void* counts, uint64_t* total,
+                             const LongList& L, cudaStream_t s) {
+    const K* keys = static_cast<const K*>(t.keys);
+    {
+        auto kern = k_probe_ranges<K, OUT, TOTAL>;
+        launch_begin("probe", s);
+        kern<<<persistent_grid(kern), PROBE_THREADS, 0, s>>>(qs, q, keys, t.offsets, t.H, (uint32_t)t.n, counts,
+                                                             total, L);
+        launch_end("probe", s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    launch_begin("long_prep", s);
+    k_long_prep<K><<<1, 1024, 0, s>>>(qs, t.offsets, t.H, (uint32_t)t.n, L);
+    launch_end("long_prep", s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto kern = k_long<K, OUT, TOTAL, false>;
+    launch_begin("long", s);
+    kern<<<persistent_grid(kern), PROBE_THREADS, 0, s>>>(qs, keys, t.values, t.offsets, t.H, (uint32_t)t.n, L, counts,
+                                                       total, nullptr, nullptr);
+    launch_end("long", s);
+    return cudaGetLastError();
 }
 
 template <typename K>
@@ -449,37 +624,28 @@ cudaError_t count_impl(const Table& t, const K* qs, uint64_t q, uint32_t* counts
     cudaError_t e = alloc_list(cap, false, s, &mem, &L);
     if (e != cudaSuccess) return e;
 
-    // Large query sets against a table larger than L2: group the queries by
-    // coarse bucket range first (the paper's query-side HashGraph, Sec. 3.3,
-    // reduced to the grouping step), so that every range's slice of the table
-    // is probed while it sits in L2; then restore slot order.
-    uint32_t shift = 0, ncoarse = 0;
-    void* pmem = nullptr;
-    if (probe_partition_plan(t, q, &shift, &ncoarse)) {
-        auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-        const size_t o_pos = al(q * sizeof(K));
-        const size_t o_cs = o_pos + (counts ? al(q * 4) : 0);
-        const size_t bytes = o_cs + (counts ? al(q * 4) : 0);
-        e = dev_alloc(&pmem, bytes, s);
+    // Large query sets against a table larger than L2: build the query-side
+    // grouping of the paper's query method (Sec. 3.3: queries bucketed like the
+    // table, each group answered against its own slice of the table), probe
+    // group by group while the slice sits in L1, then put counts back in slot order.
+    if (probe_grouping_pays(t, q)) {
+        GroupedQueries g;
+        e = group_queries(t, qs, q, &g, s);
+        void* cmem = nullptr;
+        const size_t cbytes = ((q + 4) * 4 + 255) & ~size_t(255);
+        if (e == cudaSuccess) e = dev_alloc(&cmem, 256 + (counts ? 2 * cbytes : 0), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cmem, 0, 256, s);
         if (e == cudaSuccess) {
-            char* b = static_cast<char*>(pmem);
-            K* q_sorted = reinterpret_cast<K*>(b);
-            uint32_t* pos = counts ? reinterpret_cast<uint32_t*>(b + o_pos) : nullptr;
-            uint32_t* cs = counts ? reinterpret_cast<uint32_t*>(b + o_cs) : nullptr;
-            e = partition_queries(t, qs, q, shift, ncoarse, q_sorted, pos, s);
-            if (e == cudaSuccess) {
-                if (counts && total) e = run_probe<K, OUT_U32, true, false>(t, q_sorted, q, cs, total, L, nullptr, nullptr, s);
-                else if (counts) e = run_probe<K, OUT_U32, false, false>(t, q_sorted, q, cs, nullptr, L, nullptr, nullptr, s);
-                else e = run_probe<K, OUT_NONE, true, false>(t, q_sorted, q, nullptr, total, L, nullptr, nullptr, s);
-            }
-            if (e == cudaSuccess && counts) {
-                launch_begin("unpermute", s);
-                k_unpermute<<<num_sms() * 8, PROBE_THREADS, 0, s>>>(cs, pos, q, counts);
-                launch_end("unpermute", s);
-                e = cudaGetLastError();
-            }
-            dev_free(pmem, s);
+            uint32_t* work_ctr = static_cast<uint32_t*>(cmem);
+            uint32_t* cs = counts ? reinterpret_cast<uint32_t*>(static_cast<char*>(cmem) + 256) : nullptr;
+            uint32_t* tmp = counts ? cs + cbytes / 4 : nullptr;
+            if (counts && total) e = run_probe_bins<K, OUT_U32, true>(t, g, cs, total, L, work_ctr, s);
+            else if (counts) e = run_probe_bins<K, OUT_U32, false>(t, g, cs, nullptr, L, work_ctr, s);
+            else e = run_probe_bins<K, OUT_NONE, true>(t, g, nullptr, total, L, work_ctr, s);
+            if (e == cudaSuccess && counts) e = ungroup_counts(t, &g, cs, tmp, counts, s);
         }
+        if (cmem) dev_free(cmem, s);
+        group_release(&g, s);
         dev_free(mem, s);
         return e;
     }

@@ -240,13 +240,19 @@ def _probe_only(hg, keys, B, queries, values=None):
         hg.hg_sync(t)
 
 
-def test_grouped_probe_zipf_u32(hg):
-    # table of 48 MB (> the 40 MB range size): queries are grouped by coarse
-    # bucket range before probing, then counts return to slot order
-    wl = W.zipf_large(n=1 << 23, num_buckets=1 << 22, q=(1 << 21) + 3, M=1 << 18, salt=8)
+def test_grouped_probe_zipf_u32_two_passes(hg):
+    # table > 48 MB (not L2-resident): queries are grouped by table bin in two
+    # partition passes, probed bin by bin, and the counts return to slot order
+    wl = W.zipf_large(n=(1 << 23) + 11, num_buckets=1 << 22, q=(1 << 21) + 3, M=1 << 18, salt=8)
     _probe_only(hg, wl.keys, 1 << 22, wl.queries)
 
 
+def test_grouped_probe_one_pass(hg):
+    # 2^20 buckets = 128 bins: the grouping takes a single partition pass
+    wl = W.plain_uniform((1 << 24) + 5, (1 << 20) + 7, num_buckets=1 << 20, salt=12)
+    _probe_only(hg, wl.keys, 1 << 20, wl.queries)
+
+
 def test_grouped_probe_u64(hg):
-    wl = W.join_kv(n=1 << 22, num_buckets=(1 << 22) - 9, q=(1 << 21) + 1, salt=10)
+    wl = W.join_kv(n=(1 << 22) + (1 << 20), num_buckets=(1 << 22) - 9, q=(1 << 21) + 1, salt=10)
     _probe_only(hg, wl.keys, (1 << 22) - 9, wl.queries, values=wl.values)
