@@ -532,6 +532,7 @@ k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, Chu
                const Plan* __restrict__ plan, const uint32_t* __restrict__ dr_in, const uint2* __restrict__ tile_lb,
                uint32_t* err) {
     constexpr int TILE = PassCfg<K>::TILE;
+    constexpr int PER = TILE / PASS_THREADS;
     __shared__ uint32_t s_val[TILE];
     __shared__ uint8_t s_dig[TILE];
     __shared__ uint2 s_lb[RADIX];
@@ -541,37 +542,52 @@ k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, Chu
     uint32_t seg, first;
     uint64_t lo, hi;
     chunk_range(cm, c, seg, first, lo, hi);
+    // records of the first tile; later tiles' records are fetched while the current one is processed
+    uint32_t drs[PER];
+    uint2 lbr = make_uint2(0, 0);
+    auto fetch = [&](uint64_t t0) {
+        const uint32_t cnt = (uint32_t)min((uint64_t)TILE, hi - t0);
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t li = threadIdx.x + j * PASS_THREADS;
+            drs[j] = li < cnt ? __ldg(dr_in + t0 + li) : 0xffffffffu;
+        }
+        if (threadIdx.x < RADIX)
+            lbr = __ldg(tile_lb + ((uint64_t)c * TILES_PER_CHUNK + (t0 - lo) / TILE) * RADIX + threadIdx.x);
+    };
+    if (lo < hi) fetch(lo);
     for (uint64_t t0 = lo; t0 < hi; t0 += TILE) {
         const uint32_t cnt_tile = (uint32_t)min((uint64_t)TILE, hi - t0);
-        if (threadIdx.x < RADIX)
-            s_lb[threadIdx.x] = tile_lb[((uint64_t)c * TILES_PER_CHUNK + (t0 - lo) / TILE) * RADIX + threadIdx.x];
+        if (threadIdx.x < RADIX) s_lb[threadIdx.x] = lbr;
         __syncthreads();
         // every element marks its staging position with its digit ...
-        uint32_t drs[TILE / PASS_THREADS];
+        uint32_t pj[PER];
 #pragma unroll
-        for (int j = 0; j < TILE / PASS_THREADS; ++j) {
-            const uint32_t li = threadIdx.x + j * PASS_THREADS;
-            drs[j] = li < cnt_tile ? dr_in[t0 + li] : 0xffffffffu;
+        for (int j = 0; j < PER; ++j) {
+            pj[j] = 0xffffffffu;
             if (drs[j] != 0xffffffffu) {
                 const uint32_t p = s_lb[drs[j] & 0xffu].x + (drs[j] >> 8);
-                if (p < (uint32_t)TILE) s_dig[p] = (uint8_t)(drs[j] & 0xffu);
-                else atomicOr(err, DEVERR_BOUNDS);
+                if (p < (uint32_t)TILE) {
+                    s_dig[p] = (uint8_t)(drs[j] & 0xffu);
+                    pj[j] = p;
+                } else {
+                    atomicOr(err, DEVERR_BOUNDS);
+                }
             }
         }
         __syncthreads();
         // ... so that the tile's runs are read back contiguously in staging order
         for (uint32_t i = threadIdx.x; i < cnt_tile; i += PASS_THREADS) {
             const uint2 lb = s_lb[s_dig[i]];
-            s_val[i] = src[lb.y + (i - lb.x)];
+            s_val[i] = __ldg(src + lb.y + (i - lb.x));
         }
         __syncthreads();
+        const uint64_t t1 = t0 + TILE;
+        if (t1 < hi) fetch(t1);
 #pragma unroll
-        for (int j = 0; j < TILE / PASS_THREADS; ++j) {
+        for (int j = 0; j < PER; ++j) {
             const uint32_t li = threadIdx.x + j * PASS_THREADS;
-            if (drs[j] != 0xffffffffu) {
-                const uint32_t p = s_lb[drs[j] & 0xffu].x + (drs[j] >> 8);
-                if (p < (uint32_t)TILE) dst[t0 + li] = s_val[p];
-            }
+            if (pj[j] != 0xffffffffu) dst[t0 + li] = s_val[pj[j]];
         }
         __syncthreads();
     }
