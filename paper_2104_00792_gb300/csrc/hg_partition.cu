@@ -415,7 +415,7 @@ __device__ __forceinline__ void load_tile(const K* __restrict__ in, const uint32
 // digit) in dr_out (input order) and each tile's (loc, base) per digit in
 // tile_lb[c * TILES_PER_CHUNK + tile][RADIX].
 template <typename K, int PM, bool DR = false>
-__global__ void __launch_bounds__(PASS_THREADS, 2)
+__global__ void __launch_bounds__(PASS_THREADS, 3)
 k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_t n, Hasher H, uint32_t dig_shift,
             uint32_t dig_mask, uint32_t R, ChunkMap cm, uint32_t nch_host, const Plan* __restrict__ plan,
             const uint32_t* __restrict__ chunk_base, K* __restrict__ out, uint32_t* __restrict__ out_v,
@@ -527,7 +527,7 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
 // staging order, then every element takes its value from its recorded
 // (rank, digit) and writes it in input order.
 template <typename K>
-__global__ void __launch_bounds__(PASS_THREADS, 2)
+__global__ void __launch_bounds__(PASS_THREADS, 3)
 k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, ChunkMap cm, uint32_t nch_host,
                const Plan* __restrict__ plan, const uint32_t* __restrict__ dr_in, const uint2* __restrict__ tile_lb,
                uint32_t* err) {
