@@ -316,10 +316,15 @@ def run_ours(args, rank, world, local_rank):
         "bin_build": 2 * k * N + o * (B + 1),         # per-bin counting sort: keys in, keys + offsets out
         "q_part_count": k * Q,
         "q_partition": 2 * k * Q + 4 * Q,             # queries grouped + their positions
-        "probe": k * Q + 8 * Q + k * (W - WL) + 4 * Q,
+        "probe": k * Q + 8 * Q + k * (W - WL) + 4 * Q,   # direct probe (tables that stay in L2)
         "long": k * WL,
-        "unpermute": 12 * Q,                          # positions, gathered counts, counts out
     }
+    if prof.get("q_partition", (0, 0))[0]:
+        # queries grouped by table bin: the probe kernel reads the grouped queries,
+        # each bin's offsets and keys once (into shared memory) and writes the counts
+        model["probe"] = k * Q + 4 * (B + 1) + k * N + 4 * Q
+        model["chunk_count"] = k * N                   # (same for the query side: Q = N here)
+        model["q_reverse"] = 12 * Q                    # ranks, grouped counts in, counts out
     # the method's own byte model for the whole step (build + probe; offsets 4 B)
     step_model = (3 * k) * N + 16 * B + (k + 12) * Q + k * W
     per_kernel = {}
