@@ -226,8 +226,9 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const void* d_value
     t->seed = cfg->seed;
     t->H = make_hasher(cfg->key_bytes, cfg->num_buckets, cfg->seed);
 
-    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&t->offsets), (t->B + 1) * sizeof(uint32_t), st);
-    if (e == cudaSuccess) e = dev_alloc(&t->keys, n * t->key_bytes, st);
+    // 16 spare bytes after offsets and keys: bulk copies of a bin may round their end up to 16 bytes
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&t->offsets), (t->B + 1) * sizeof(uint32_t) + 16, st);
+    if (e == cudaSuccess) e = dev_alloc(&t->keys, n * t->key_bytes + 16, st);
     if (e == cudaSuccess && t->has_values) e = dev_alloc(reinterpret_cast<void**>(&t->values), n * 4, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void**>(&t->err), sizeof(uint32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->err, 0, sizeof(uint32_t), st);

@@ -460,47 +460,87 @@ k_probe_ranges(const K* __restrict__ qs, uint64_t q, const K* __restrict__ keys,
 }
 
 // One table bin per CTA work item (the paper's per-bucket intersection,
-// Sec. 3.3, done a bin of 8192 buckets at a time): the bin's offsets and, when
-// they fit, its keys are copied into shared memory with coalesced loads, then
-// the bin's grouped queries are answered from shared memory.  Buckets longer
-// than WALK_WARP keys go to the long-bucket list as in the direct probe.
-constexpr uint32_t BIN_KEY_BYTES = 64 * 1024;
-constexpr int BIN_PROBE_THREADS = 512;
+// Sec. 3.3, done a bin of 8192 buckets at a time).  The bin's offsets and
+// (when they fit) keys are brought into shared memory by bulk copies (TMA)
+// while the previous bin's queries are answered from the other buffer, so the
+// copies overlap the work.  Buckets longer than WALK_WARP keys go to the
+// long-bucket list as in the direct probe; a bin whose keys do not fit is
+// walked in global memory.  Every wait on a copy is bounded.
+constexpr uint32_t BIN_KEY_BYTES = 80 * 1024;                                  // per buffer
+constexpr uint32_t BIN_OFF_BYTES = ((BIN_BUCKETS + 1) * 4 + 15) / 16 * 16;     // 8193 offsets, rounded to 16 B
+constexpr uint32_t BIN_BUF_BYTES = BIN_OFF_BYTES + BIN_KEY_BYTES;
+constexpr int BIN_PROBE_THREADS = 1024;
+constexpr uint32_t COPY_WAIT_LIMIT = 1u << 26;  // polls of a copy's barrier (far beyond any real copy)
 
 template <typename K, int OUT, bool TOTAL>
-__global__ void __launch_bounds__(BIN_PROBE_THREADS, 2)
+__global__ void __launch_bounds__(BIN_PROBE_THREADS, 1)
 k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, uint32_t nbins,
              const K* __restrict__ keys, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
-             uint64_t* total, LongList L, uint32_t* work_ctr) {
-    constexpr uint32_t KCAP = BIN_KEY_BYTES / sizeof(K);
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* s_off = reinterpret_cast<uint32_t*>(smem);                       // BIN_BUCKETS + 1
-    K* s_keys = reinterpret_cast<K*>(smem + ((BIN_BUCKETS + 1) * 4 + 15) / 16 * 16);
-    __shared__ uint32_t s_item;
+             uint64_t* total, LongList L, uint32_t* work_ctr, uint32_t* err) {
+    constexpr uint32_t KVEC = 16 / sizeof(K);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_bin[2], s_k0[2], s_klo[2], s_staged[2];
     const unsigned lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint64_t B = H.B;
     uint64_t acc = 0;
-    while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(work_ctr, 1u);
-        __syncthreads();
-        const uint32_t p = s_item;
-        if (p >= nbins) break;
-        const uint32_t q0 = qbin_start[p], q1 = qbin_start[p + 1];
-        if (q0 == q1) {
-            __syncthreads();
-            continue;
-        }
+
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // thread 0: claim the next bin and start its copies into buffer b
+    auto issue = [&](int b) {
+        const uint32_t p = atomicAdd(work_ctr, 1u);
+        s_bin[b] = p;
+        if (p >= nbins) return;
         const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
         const uint32_t nb = (uint32_t)min((uint64_t)BIN_BUCKETS, B - b0);
-        for (uint32_t j = threadIdx.x; j <= nb; j += blockDim.x) s_off[j] = min(__ldg(offs + b0 + j), n_keys);
+        const uint32_t k0 = min(__ldg(offs + b0), n_keys);
+        const uint32_t k1 = max(k0, min(__ldg(offs + b0 + nb), n_keys));
+        const uint32_t klo = k0 & ~(KVEC - 1);
+        const uint32_t off_bytes = ((nb + 1) * 4 + 15) & ~15u;
+        const uint32_t key_bytes = (uint32_t)((((uint64_t)(k1 - klo)) * sizeof(K) + 15) & ~15ull);
+        const bool staged = (uint64_t)(k1 - klo) * sizeof(K) <= BIN_KEY_BYTES;
+        s_k0[b] = k0;
+        s_klo[b] = klo;
+        s_staged[b] = staged;
+        unsigned char* buf = smem + (size_t)b * BIN_BUF_BYTES;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar[b], off_bytes + (staged ? key_bytes : 0u));
+        bulk_load(buf, offs + b0, off_bytes, &s_bar[b]);
+        if (staged && key_bytes) bulk_load(buf + BIN_OFF_BYTES, keys + klo, key_bytes, &s_bar[b]);
+    };
+    if (threadIdx.x == 0) issue(0);
+    uint32_t phase0 = 0, phase1 = 0;
+    int cur = 0;
+    bool failed = false;
+    while (true) {
+        if (threadIdx.x == 0) issue(cur ^ 1);  // the previous user of that buffer finished at the last barrier
         __syncthreads();
-        const uint32_t k0 = s_off[0], k1 = max(k0, s_off[nb]);
-        const bool staged = k1 - k0 <= KCAP;
-        if (staged)
-            for (uint32_t i = threadIdx.x; i < k1 - k0; i += blockDim.x) s_keys[i] = __ldg(keys + k0 + i);
-        __syncthreads();
-        const K* kb = staged ? s_keys : keys + k0;  // keys of the bin, indexed from k0
+        const uint32_t p = s_bin[cur];
+        if (p >= nbins) break;
+        {
+            const uint32_t ph = cur ? phase1 : phase0;
+            uint32_t polls = 0;
+            while (!mbar_test_parity(&s_bar[cur], ph) && ++polls < COPY_WAIT_LIMIT) {
+            }
+            failed = polls >= COPY_WAIT_LIMIT;
+            if (cur) phase1 ^= 1; else phase0 ^= 1;
+        }
+        if (__syncthreads_or(failed)) break;
+        const uint32_t* s_off = reinterpret_cast<const uint32_t*>(smem + (size_t)cur * BIN_BUF_BYTES);
+        const uint32_t k0 = s_k0[cur];
+        const bool staged = s_staged[cur] != 0;
+        const K* kb = staged ? reinterpret_cast<const K*>(smem + (size_t)cur * BIN_BUF_BYTES + BIN_OFF_BYTES) +
+                                   (k0 - s_klo[cur])
+                             : keys + k0;  // keys of the bin, indexed from k0
+        const uint32_t q0 = qbin_start[p], q1 = qbin_start[p + 1];
+        const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
+        const uint32_t nb = (uint32_t)min((uint64_t)BIN_BUCKETS, B - b0);
         for (uint32_t i0 = q0 + warp * 32; i0 < q1; i0 += nwarps * 32) {
             const uint32_t i = i0 + lane;
             const bool ok = i < q1;
@@ -509,8 +549,8 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
             if (ok) {
                 uint32_t j = bucket_of(key, H) - (uint32_t)b0;
                 if (j >= nb) j = nb - 1;  // queries of this bin hash into it by construction
-                lo = s_off[j] - k0;
-                hi = max(s_off[j + 1], s_off[j]) - k0;
+                lo = min(s_off[j], n_keys) - k0;
+                hi = max(min(s_off[j + 1], n_keys) - k0, lo);
             }
             const uint32_t len = hi - lo;
             uint8_t cls = !ok ? CLS_NONE : len <= WALK_LANE ? CLS_LANE : len <= WALK_WARP ? CLS_WARP : CLS_LONG;
@@ -549,6 +589,22 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
             }
         }
         __syncthreads();
+        cur ^= 1;
+    }
+    if (failed) {
+        // a copy never completed (not expected): record it, give the other buffer's
+        // copy a bounded chance to land, and leave
+        if (threadIdx.x == 0) {
+            atomicOr(err, DEVERR_TIMEOUT);
+            const int other = cur ^ 1;
+            if (s_bin[other] < nbins) {
+                const uint32_t ph = other ? phase1 : phase0;
+                uint32_t polls = 0;
+                while (!mbar_test_parity(&s_bar[other], ph) && ++polls < COPY_WAIT_LIMIT) {
+                }
+            }
+        }
+        return;
     }
     if (TOTAL) {
         const uint64_t sum = block_sum(acc);
@@ -563,7 +619,7 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
     const K* qs = static_cast<const K*>(g.q_grouped);
     {
         auto kern = k_probe_bins<K, OUT, TOTAL>;
-        const size_t smem = ((BIN_BUCKETS + 1) * 4 + 15) / 16 * 16 + BIN_KEY_BYTES;
+        const size_t smem = 2 * (size_t)BIN_BUF_BYTES;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
@@ -572,7 +628,7 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
             per_sm = 1;
         launch_begin("probe", s);
         kern<<<num_sms() * per_sm, BIN_PROBE_THREADS, smem, s>>>(qs, g.bin_start, g.nbins, keys, t.offsets, t.H,
-                                                                 (uint32_t)t.n, counts, total, L, work_ctr);
+                                                                 (uint32_t)t.n, counts, total, L, work_ctr, t.err);
         launch_end("probe", s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
