@@ -541,10 +541,16 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
         const uint32_t q0 = qbin_start[p], q1 = qbin_start[p + 1];
         const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
         const uint32_t nb = (uint32_t)min((uint64_t)BIN_BUCKETS, B - b0);
+        // each warp answers 32 queries at a time; the next 32 are loaded meanwhile
+        K key_next = (q0 + warp * 32 + lane < q1) ? __ldg(qs + q0 + warp * 32 + lane) : (K)0;
         for (uint32_t i0 = q0 + warp * 32; i0 < q1; i0 += nwarps * 32) {
             const uint32_t i = i0 + lane;
             const bool ok = i < q1;
-            const K key = ok ? qs[i] : (K)0;
+            const K key = key_next;
+            {
+                const uint32_t inext = i + nwarps * 32;
+                key_next = inext < q1 ? __ldg(qs + inext) : (K)0;
+            }
             uint32_t lo = 0, hi = 0;
             if (ok) {
                 uint32_t j = bucket_of(key, H) - (uint32_t)b0;
