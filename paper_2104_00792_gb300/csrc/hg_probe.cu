@@ -30,12 +30,25 @@ enum : uint8_t { CLS_NONE = 0, CLS_LANE = 1, CLS_WARP = 2, CLS_LONG = 3 };
 
 struct LongList {
     uint32_t* n;             // entries appended (may exceed cap)
+    uint32_t* n_uniq;        // entries that are walked (written by k_long_prep)
     uint64_t* total_chunks;  // written by k_long_prep
     uint32_t* slot;          // [cap] query slot of each entry
-    uint64_t* chunk_start;   // [cap] exclusive prefix of chunk counts
+    uint64_t* chunk_start;   // [cap] exclusive prefix of chunk counts, over the walked entries
+    uint32_t* uniq;          // [cap] walked entries (each distinct query key once when deduplicated)
+    uint32_t* rep;           // [cap] entry whose walk answers entry e
+    uint32_t* mult;          // [cap] number of entries a walked entry answers
     uint32_t* cursor;        // [cap] gather write cursors (or null)
     uint32_t cap;
 };
+constexpr uint32_t DEDUP_SLOTS = 16384;  // shared-memory hash table of k_long_prep
+
+// The part of a LongList the probe kernels append to.
+struct LongSink {
+    uint32_t* n;
+    uint32_t* slot;
+    uint32_t cap;
+};
+inline LongSink sink_of(const LongList& L) { return LongSink{L.n, L.slot, L.cap}; }
 
 template <typename K>
 __device__ __forceinline__ uint32_t lane_count(const K* __restrict__ keys, uint32_t lo, uint32_t hi, K key) {
@@ -107,7 +120,7 @@ template <typename K, int OUT, bool GATHER>
 __device__ __forceinline__ void probe_group(const uint64_t (&slot)[KeyVec<K>::N], const bool (&valid)[KeyVec<K>::N],
                                             const K (&qk)[KeyVec<K>::N], const K* __restrict__ keys,
                                             const uint32_t* __restrict__ vals, const uint32_t* __restrict__ offs,
-                                            const Hasher& H, uint32_t n_keys, void* counts, const LongList& L,
+                                            const Hasher& H, uint32_t n_keys, void* counts, const LongSink& L,
                                             const uint64_t* __restrict__ out_offs, uint32_t* out_vals,
                                             uint64_t& acc) {
     constexpr int VEC = KeyVec<K>::N;
@@ -200,7 +213,7 @@ template <typename K, int OUT, bool TOTAL, bool GATHER>
 __global__ void __launch_bounds__(PROBE_THREADS)
 k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, const K* __restrict__ keys,
         const uint32_t* __restrict__ vals, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
-        uint64_t* total, LongList L, const uint64_t* __restrict__ out_offs, uint32_t* out_vals) {
+        uint64_t* total, LongSink L, const uint64_t* __restrict__ out_offs, uint32_t* out_vals) {
     constexpr int VEC = KeyVec<K>::N;
     const unsigned lane = lane_id();
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -239,21 +252,81 @@ k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, cons
     }
 }
 
-// One block: chunk_start[e] = sum of ceil(len / LONG_CHUNK) over entries before e.
-template <typename K>
+// One block.  With DEDUP (32-bit keys), entries whose query keys are equal
+// (hence in the same bucket, with the same count) are grouped through a
+// shared-memory hash table: only the first of each group is walked, and the
+// others copy its count afterwards (the list intersection of Sec. 3.3 matches
+// each distinct query key of a bucket once).  Then
+// chunk_start[u] = sum of ceil(len / LONG_CHUNK) over walked entries before u.
+template <typename K, bool DEDUP>
 __global__ void __launch_bounds__(1024)
 k_long_prep(const K* __restrict__ qs, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, LongList L) {
+    extern __shared__ unsigned long long s_ht[];  // DEDUP: (entry << 32 | key), all ones = empty
     __shared__ uint64_t s_warp[32];
     __shared__ uint64_t s_total;
+    __shared__ uint32_t s_wu[32], s_tu;
     const uint32_t n = min(*L.n, L.cap);
     const unsigned lane = lane_id();
     const int w = threadIdx.x >> 5;
-    uint64_t running = 0;
+    if (DEDUP) {
+        for (uint32_t i = threadIdx.x; i < DEDUP_SLOTS; i += blockDim.x) s_ht[i] = ~0ull;
+        __syncthreads();
+        for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const uint32_t key = (uint32_t)qs[L.slot[e]];
+            uint32_t h = fmix32(key ^ 0x9e3779b9u) & (DEDUP_SLOTS - 1);
+            uint32_t r = e;
+            for (uint32_t probe = 0; probe < DEDUP_SLOTS; ++probe) {
+                unsigned long long wv = s_ht[h];
+                if (wv == ~0ull) {
+                    wv = atomicCAS(&s_ht[h], ~0ull, ((unsigned long long)e << 32) | key);
+                    if (wv == ~0ull) break;  // this entry heads its group
+                }
+                if ((uint32_t)wv == key) {
+                    r = (uint32_t)(wv >> 32);
+                    break;
+                }
+                h = (h + 1) & (DEDUP_SLOTS - 1);
+            }
+            L.rep[e] = r;  // a full table leaves r = e: the entry is walked on its own
+        }
+        __syncthreads();
+        for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
+            if (L.rep[e] == e) L.mult[e] = 1;
+        __syncthreads();
+        for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
+            if (L.rep[e] != e) atomicAdd(L.mult + L.rep[e], 1u);
+    }
+    // list of walked entries (block-wide compaction, input order)
+    uint32_t nu = 0;
     for (uint32_t base = 0; base < n; base += blockDim.x) {
         const uint32_t e = base + threadIdx.x;
+        const uint32_t u = (e < n && (!DEDUP || L.rep[e] == e)) ? 1u : 0u;
+        const uint32_t incl = warp_inclusive_scan(u);
+        if (lane == 31) s_wu[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t wv = lane < (blockDim.x >> 5) ? s_wu[lane] : 0;
+            const uint32_t wi = warp_inclusive_scan(wv);
+            if (lane < (blockDim.x >> 5)) s_wu[lane] = wi - wv;
+            if (lane == 31) s_tu = wi;
+        }
+        __syncthreads();
+        if (u) {
+            L.uniq[nu + s_wu[w] + incl - u] = e;
+            if (!DEDUP) {
+                L.rep[e] = e;
+                L.mult[e] = 1;
+            }
+        }
+        nu += s_tu;
+        __syncthreads();
+    }
+    uint64_t running = 0;
+    for (uint32_t base = 0; base < nu; base += blockDim.x) {
+        const uint32_t u = base + threadIdx.x;
         uint64_t ch = 0;
-        if (e < n) {
-            const uint32_t b = bucket_of(qs[L.slot[e]], H);
+        if (u < nu) {
+            const uint32_t b = bucket_of(qs[L.slot[L.uniq[u]]], H);
             const uint32_t hi = min(offs[b + 1], n_keys);
             const uint32_t lo = min(offs[b], hi);
             ch = (hi - lo + LONG_CHUNK - 1) / LONG_CHUNK;
@@ -268,14 +341,17 @@ k_long_prep(const K* __restrict__ qs, const uint32_t* __restrict__ offs, Hasher 
             if (lane == 31) s_total = wi;
         }
         __syncthreads();
-        if (e < n) L.chunk_start[e] = running + s_warp[w] + incl - ch;
+        if (u < nu) L.chunk_start[u] = running + s_warp[w] + incl - ch;
         running += s_total;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *L.total_chunks = running;
+    if (threadIdx.x == 0) {
+        *L.total_chunks = running;
+        *L.n_uniq = nu;
+    }
 }
 
-// Long buckets, one LONG_CHUNK-key chunk per warp iteration.
+// Long buckets, one LONG_CHUNK-key chunk per warp iteration, over the walked entries.
 template <typename K, int OUT, bool TOTAL, bool GATHER>
 __global__ void __launch_bounds__(PROBE_THREADS)
 k_long(const K* __restrict__ qs, const K* __restrict__ keys, const uint32_t* __restrict__ vals,
@@ -285,22 +361,23 @@ k_long(const K* __restrict__ qs, const K* __restrict__ keys, const uint32_t* __r
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nchunks = *L.total_chunks;
-    const uint32_t n = min(*L.n, L.cap);
+    const uint32_t nu = *L.n_uniq;
     uint64_t acc = 0;
     for (uint64_t c = gw; c < nchunks; c += nw) {
-        // entry e: the last with chunk_start[e] <= c
-        uint32_t lo = 0, hi = n;
+        // walked entry u: the last with chunk_start[u] <= c
+        uint32_t lo = 0, hi = nu;
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
             if (L.chunk_start[mid] <= c) lo = mid; else hi = mid;
         }
-        const uint32_t e = lo;
+        const uint32_t u = lo;
+        const uint32_t e = L.uniq[u];
         const uint32_t s = L.slot[e];
         const K key = qs[s];
         const uint32_t b = bucket_of(key, H);
         const uint64_t l1 = min(offs[b + 1], n_keys);
         const uint64_t l0 = min((uint64_t)offs[b], l1);
-        const uint64_t p0 = l0 + (c - L.chunk_start[e]) * LONG_CHUNK;
+        const uint64_t p0 = l0 + (c - L.chunk_start[u]) * LONG_CHUNK;
         const uint64_t p1 = min(l1, p0 + LONG_CHUNK);
         const uint32_t cnt = warp_count(keys, p0, p1, key);
         if (!GATHER) {
@@ -308,7 +385,7 @@ k_long(const K* __restrict__ qs, const K* __restrict__ keys, const uint32_t* __r
                 if (OUT == OUT_U32) atomicAdd(static_cast<uint32_t*>(counts) + s, cnt);
                 if (OUT == OUT_U64)
                     atomicAdd(reinterpret_cast<unsigned long long*>(counts) + s, (unsigned long long)cnt);
-                acc += cnt;
+                acc += (uint64_t)cnt * L.mult[e];
             }
         } else if (cnt) {
             uint32_t base = 0;
@@ -323,6 +400,19 @@ k_long(const K* __restrict__ qs, const K* __restrict__ keys, const uint32_t* __r
     }
 }
 
+// Entries answered by another entry's walk copy its (now final) count.
+template <int OUT>
+__global__ void __launch_bounds__(PROBE_THREADS)
+k_long_copy(LongList L, void* counts) {
+    const uint32_t n = min(*L.n, L.cap);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const uint32_t r = L.rep[e];
+        if (r == e) continue;
+        if (OUT == OUT_U32) static_cast<uint32_t*>(counts)[L.slot[e]] = static_cast<uint32_t*>(counts)[L.slot[r]];
+        if (OUT == OUT_U64) static_cast<uint64_t*>(counts)[L.slot[e]] = static_cast<uint64_t*>(counts)[L.slot[r]];
+    }
+}
+
 template <typename Kern>
 unsigned persistent_grid(Kern kern) {
     int per_sm = 0;
@@ -331,21 +421,52 @@ unsigned persistent_grid(Kern kern) {
     return (unsigned)(num_sms() * per_sm);
 }
 
+// Scratch layout of a long-bucket list with `cap` entries (16-byte header, then arrays).
+void map_list(void* mem, uint32_t cap, bool with_cursor, LongList* L) {
+    char* p = static_cast<char*>(mem);
+    L->n = reinterpret_cast<uint32_t*>(p);
+    L->n_uniq = reinterpret_cast<uint32_t*>(p + 4);
+    L->total_chunks = reinterpret_cast<uint64_t*>(p + 8);
+    L->chunk_start = reinterpret_cast<uint64_t*>(p + 16);
+    L->slot = reinterpret_cast<uint32_t*>(p + 16 + (size_t)cap * 8);
+    L->uniq = L->slot + cap;
+    L->rep = L->uniq + cap;
+    L->mult = L->rep + cap;
+    L->cursor = with_cursor ? L->mult + cap : nullptr;
+    L->cap = cap;
+}
+
 cudaError_t alloc_list(uint32_t cap, bool with_cursor, cudaStream_t s, void** mem, LongList* L) {
-    const size_t hdr = 16;
-    const size_t bytes = hdr + (size_t)cap * (sizeof(uint32_t) + sizeof(uint64_t) + (with_cursor ? 4 : 0)) + 16;
+    const size_t bytes = 16 + (size_t)cap * (8 + 16 + (with_cursor ? 4 : 0)) + 16;
     cudaError_t e = dev_alloc(mem, bytes, s);
     if (e != cudaSuccess) return e;
-    char* p = static_cast<char*>(*mem);
-    L->n = reinterpret_cast<uint32_t*>(p);
-    L->total_chunks = reinterpret_cast<uint64_t*>(p + 8);
-    L->chunk_start = reinterpret_cast<uint64_t*>(p + hdr);
-    L->slot = reinterpret_cast<uint32_t*>(p + hdr + (size_t)cap * 8);
-    L->cursor = with_cursor ? L->slot + cap : nullptr;
-    L->cap = cap;
-    e = cudaMemsetAsync(p, 0, hdr, s);
+    map_list(*mem, cap, with_cursor, L);
+    e = cudaMemsetAsync(*mem, 0, 16, s);
     if (e == cudaSuccess && with_cursor) e = cudaMemsetAsync(L->cursor, 0, (size_t)cap * 4, s);
     return e;
+}
+
+// Prepares the long-bucket walk (deduplicated when allowed, for 32-bit keys).
+template <typename K, bool ALLOW_DEDUP>
+cudaError_t launch_long_prep(const Table& t, const K* qs, const LongList& L, cudaStream_t s) {
+    constexpr bool DEDUP = sizeof(K) == 4 && ALLOW_DEDUP;
+    auto kern = k_long_prep<K, DEDUP>;
+    const size_t smem = DEDUP ? DEDUP_SLOTS * sizeof(unsigned long long) : 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    launch_begin("long_prep", s);
+    kern<<<1, 1024, smem, s>>>(qs, t.offsets, t.H, (uint32_t)t.n, L);
+    launch_end("long_prep", s);
+    return cudaGetLastError();
+}
+
+template <int OUT>
+cudaError_t launch_long_copy(const LongList& L, void* counts, cudaStream_t s) {
+    if (OUT == OUT_NONE) return cudaSuccess;
+    launch_begin("long", s);
+    k_long_copy<OUT><<<num_sms() * 2, PROBE_THREADS, 0, s>>>(L, counts);
+    launch_end("long", s);
+    return cudaGetLastError();
 }
 
 template <typename K>
@@ -370,16 +491,15 @@ cudaError_t run_probe(const Table& t, const K* qs, uint64_t q, void* counts, uin
         if (need < g) g = (unsigned)(need < 1 ? 1 : need);
         launch_begin(GATHER ? "gather" : "probe", s);
         kern<<<g, PROBE_THREADS, 0, s>>>(qs, q, head, nvec, keys, t.values, t.offsets, t.H, (uint32_t)t.n, counts,
-                                         total, L, out_offs, out_vals);
+                                         total, sink_of(L), out_offs, out_vals);
         launch_end(GATHER ? "gather" : "probe", s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (!GATHER) {
-        launch_begin("long_prep", s);
-        k_long_prep<K><<<1, 1024, 0, s>>>(qs, t.offsets, t.H, (uint32_t)t.n, L);
-        launch_end("long_prep", s);
-        cudaError_t e = cudaGetLastError();
+        // counts feeding a gather (OUT_U64) keep one walk per entry: the gather's
+        // second phase walks every entry itself
+        cudaError_t e = launch_long_prep<K, OUT != OUT_U64>(t, qs, L, s);
         if (e != cudaSuccess) return e;
     }
     auto kern = k_long<K, OUT, TOTAL, GATHER>;
@@ -387,7 +507,9 @@ cudaError_t run_probe(const Table& t, const K* qs, uint64_t q, void* counts, uin
     kern<<<persistent_grid(kern), PROBE_THREADS, 0, s>>>(qs, keys, t.values, t.offsets, t.H, (uint32_t)t.n, L,
                                                        counts, total, out_offs, out_vals);
     launch_end(GATHER ? "long_gather" : "long", s);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || GATHER || OUT == OUT_U64) return e;
+    return launch_long_copy<OUT>(L, counts, s);
 }
 
 // Byte-model helper: stats[0] += sum of walked bucket lengths, stats[1] += the
@@ -417,48 +539,6 @@ k_walk_stats(const K* __restrict__ qs, uint64_t q, const uint32_t* __restrict__ 
     }
 }
 
-// Probe over queries grouped by table bin: each CTA takes RANGE consecutive
-// grouped queries at a time, so the bins it touches (their offsets and keys,
-// about 100 KB) stay in L1 while their queries are answered.  Same per-slot
-// work as k_probe; q_grouped is padded to a multiple of 16 bytes.
-constexpr uint32_t RANGE = 8192;
-
-template <typename K, int OUT, bool TOTAL>
-__global__ void __launch_bounds__(PROBE_THREADS)
-k_probe_ranges(const K* __restrict__ qs, uint64_t q, const K* __restrict__ keys, const uint32_t* __restrict__ offs,
-               Hasher H, uint32_t n_keys, void* counts, uint64_t* total, LongList L) {
-    constexpr int VEC = KeyVec<K>::N;
-    const unsigned lane = lane_id();
-    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint64_t nranges = (q + RANGE - 1) / RANGE;
-    uint64_t acc = 0;
-    uint64_t slot[VEC];
-    bool valid[VEC];
-    K qk[VEC];
-    for (uint64_t r = blockIdx.x; r < nranges; r += gridDim.x) {
-        const uint64_t r0 = r * RANGE;
-        const uint64_t g_end = (min(q, r0 + RANGE) - r0 + VEC - 1) / VEC;  // vector groups in the range
-        for (uint64_t g0 = (uint64_t)warp * 32; g0 < g_end; g0 += (uint64_t)nwarps * 32) {
-            const uint64_t g = g0 + lane;
-            const bool ok = g < g_end;
-            KeyVec<K> kv;
-            if (ok) kv = load_keys16(qs + r0 + g * VEC);
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                slot[j] = r0 + g * VEC + j;
-                valid[j] = ok && slot[j] < q;
-                qk[j] = valid[j] ? kv.k[j] : (K)0;
-            }
-            probe_group<K, OUT, false>(slot, valid, qk, keys, nullptr, offs, H, n_keys, counts, L, nullptr, nullptr,
-                                       acc);
-        }
-    }
-    if (TOTAL) {
-        const uint64_t sum = block_sum(acc);
-        if (threadIdx.x == 0 && sum) atomicAdd(reinterpret_cast<unsigned long long*>(total), (unsigned long long)sum);
-    }
-}
-
 // One table bin per CTA work item (the paper's per-bucket intersection,
 // Sec. 3.3, done a bin of 8192 buckets at a time).  The bin's offsets and
 // (when they fit) keys are brought into shared memory by bulk copies (TMA)
@@ -476,7 +556,7 @@ template <typename K, int OUT, bool TOTAL>
 __global__ void __launch_bounds__(BIN_PROBE_THREADS, 1)
 k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, uint32_t nbins,
              const K* __restrict__ keys, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
-             uint64_t* total, LongList L, uint32_t* work_ctr, uint32_t* err) {
+             uint64_t* total, LongSink L, uint32_t* work_ctr, uint32_t* err) {
     constexpr uint32_t KVEC = 16 / sizeof(K);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -634,48 +714,21 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
             per_sm = 1;
         launch_begin("probe", s);
         kern<<<num_sms() * per_sm, BIN_PROBE_THREADS, smem, s>>>(qs, g.bin_start, g.nbins, keys, t.offsets, t.H,
-                                                                 (uint32_t)t.n, counts, total, L, work_ctr, t.err);
+                                                                 (uint32_t)t.n, counts, total, sink_of(L), work_ctr, t.err);
         launch_end("probe", s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    launch_begin("long_prep", s);
-    k_long_prep<K><<<1, 1024, 0, s>>>(qs, t.offsets, t.H, (uint32_t)t.n, L);
-    launch_end("long_prep", s);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_long_prep<K, true>(t, qs, L, s);
     if (e != cudaSuccess) return e;
     auto kern = k_long<K, OUT, TOTAL, false>;
     launch_begin("long", s);
     kern<<<persistent_grid(kern), PROBE_THREADS, 0, s>>>(qs, keys, t.values, t.offsets, t.H, (uint32_t)t.n, L, counts,
                                                        total, nullptr, nullptr);
     launch_end("long", s);
-    return cudaGetLastError();
-}
-
-template <typename K, int OUT, bool TOTAL>
-cudaError_t run_probe_ranges(const Table& t, const K* qs, uint64_t q, void* counts, uint64_t* total,
-                             const LongList& L, cudaStream_t s) {
-    const K* keys = static_cast<const K*>(t.keys);
-    {
-        auto kern = k_probe_ranges<K, OUT, TOTAL>;
-        launch_begin("probe", s);
-        kern<<<persistent_grid(kern), PROBE_THREADS, 0, s>>>(qs, q, keys, t.offsets, t.H, (uint32_t)t.n, counts,
-                                                             total, L);
-        launch_end("probe", s);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    launch_begin("long_prep", s);
-    k_long_prep<K><<<1, 1024, 0, s>>>(qs, t.offsets, t.H, (uint32_t)t.n, L);
-    launch_end("long_prep", s);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    auto kern = k_long<K, OUT, TOTAL, false>;
-    launch_begin("long", s);
-    kern<<<persistent_grid(kern), PROBE_THREADS, 0, s>>>(qs, keys, t.values, t.offsets, t.H, (uint32_t)t.n, L, counts,
-                                                       total, nullptr, nullptr);
-    launch_end("long", s);
-    return cudaGetLastError();
+    return launch_long_copy<OUT>(L, counts, s);
 }
 
 template <typename K>
@@ -757,16 +810,9 @@ cudaError_t gather_offsets(const Table& t, const void* d_q, uint64_t q, uint64_t
 cudaError_t gather_values(const Table& t, const void* d_q, uint64_t q, const uint64_t* out_offsets,
                           uint32_t* out_values, GatherCtx* ctx, cudaStream_t s) {
     if (q == 0) return cudaSuccess;
-    // Rebuild the list view over the same scratch (layout fixed by alloc_list).
+    // The list view over the same scratch (layout fixed by map_list).
     LongList L{};
-    char* p = static_cast<char*>(ctx->scratch);
-    const uint32_t cap = (uint32_t)q;
-    L.n = reinterpret_cast<uint32_t*>(p);
-    L.total_chunks = reinterpret_cast<uint64_t*>(p + 8);
-    L.chunk_start = reinterpret_cast<uint64_t*>(p + 16);
-    L.slot = reinterpret_cast<uint32_t*>(p + 16 + (size_t)cap * 8);
-    L.cursor = L.slot + cap;
-    L.cap = cap;
+    map_list(ctx->scratch, (uint32_t)q, true, &L);
     if (t.key_bytes == 4)
         return run_probe<uint32_t, OUT_NONE, false, true>(t, static_cast<const uint32_t*>(d_q), q, nullptr, nullptr, L,
                                                           out_offsets, out_values, s);

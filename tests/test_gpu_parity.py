@@ -109,6 +109,19 @@ def test_all_duplicates_one_bucket(hg):
     _run_all(hg, keys, 1 << 12, 0, queries, flags=hg.HG_INDEX_VALUES)
 
 
+def test_long_buckets_repeated_queries(hg):
+    """Every bucket is long (4 buckets, ~2^14 keys each); the queries repeat
+    20000 distinct keys one to four times in shuffled order, more distinct keys
+    than the long-bucket walk groups at once, so both the grouped walks and the
+    per-entry walks are taken."""
+    rng = np.random.default_rng(77)
+    keys = rng.integers(0, 1 << 14, size=(1 << 16) + 9, dtype=np.uint32)
+    distinct = rng.permutation(np.arange(1 << 15, dtype=np.uint32))[:20000]
+    queries = np.repeat(distinct, rng.integers(1, 5, size=distinct.size))
+    rng.shuffle(queries)
+    _run_all(hg, keys, 4, 3, queries, flags=hg.HG_INDEX_VALUES)
+
+
 def test_sequential_keys(hg):
     keys = np.arange(1, (1 << 18) + 1, dtype=np.uint32)
     queries = np.arange(0, 1 << 18, 3, dtype=np.uint32)
