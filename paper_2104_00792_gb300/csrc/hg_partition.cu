@@ -525,7 +525,9 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
 // order, dst receives the values in its input order.  Each tile reads the runs
 // it wrote (contiguous, so the reads coalesce) into shared memory in its
 // staging order, then every element takes its value from its recorded
-// (rank, digit) and writes it in input order.
+// (rank, digit) and writes it in input order.  The run reads are asynchronous
+// copies into shared memory, all of a thread's in flight at once, and the next
+// tile's records are requested while they land.
 template <typename K>
 __global__ void __launch_bounds__(PASS_THREADS, 3)
 k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, ChunkMap cm, uint32_t nch_host,
@@ -542,7 +544,6 @@ k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, Chu
     uint32_t seg, first;
     uint64_t lo, hi;
     chunk_range(cm, c, seg, first, lo, hi);
-    // records of the first tile; later tiles' records are fetched while the current one is processed
     uint32_t drs[PER];
     uint2 lbr = make_uint2(0, 0);
     auto fetch = [&](uint64_t t0) {
@@ -561,35 +562,46 @@ k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, Chu
         if (threadIdx.x < RADIX) s_lb[threadIdx.x] = lbr;
         __syncthreads();
         // every element marks its staging position with its digit ...
-        uint32_t pj[PER];
+        static_assert(TILE < 0xffff, "staging positions are kept in 16 bits");
+        uint32_t pj[PER / 2];  // two 16-bit staging positions per word, 0xffff = none
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
-            pj[j] = 0xffffffffu;
+            uint32_t pos = 0xffffu;
             if (drs[j] != 0xffffffffu) {
                 const uint32_t p = s_lb[drs[j] & 0xffu].x + (drs[j] >> 8);
                 if (p < (uint32_t)TILE) {
                     s_dig[p] = (uint8_t)(drs[j] & 0xffu);
-                    pj[j] = p;
+                    pos = p;
                 } else {
                     atomicOr(err, DEVERR_BOUNDS);
                 }
             }
+            if (j & 1) pj[j / 2] |= pos << 16;
+            else pj[j / 2] = pos;
         }
         __syncthreads();
         // ... so that the tile's runs are read back contiguously in staging order
-        for (uint32_t i = threadIdx.x; i < cnt_tile; i += PASS_THREADS) {
-            const uint2 lb = s_lb[s_dig[i]];
-            s_val[i] = __ldg(src + lb.y + (i - lb.x));
+        // (asynchronous copies straight into shared memory)
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t i = threadIdx.x + j * PASS_THREADS;
+            if (i < cnt_tile) {
+                const uint2 lb = s_lb[s_dig[i]];
+                cp_async4(s_val + i, src + lb.y + (i - lb.x));
+            }
         }
-        __syncthreads();
         const uint64_t t1 = t0 + TILE;
         if (t1 < hi) fetch(t1);
+        cp_async_wait_all();
+        __syncthreads();
+        // s_lb and s_dig are not read past this point, and s_val is next written
+        // after the next tile's second barrier, so no barrier ends the tile
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const uint32_t li = threadIdx.x + j * PASS_THREADS;
-            if (pj[j] != 0xffffffffu) dst[t0 + li] = s_val[pj[j]];
+            const uint32_t pos = (pj[j / 2] >> ((j & 1) * 16)) & 0xffffu;
+            if (pos != 0xffffu) dst[t0 + li] = s_val[pos];
         }
-        __syncthreads();
     }
 }
 
