@@ -545,12 +545,19 @@ k_walk_stats(const K* __restrict__ qs, uint64_t q, const uint32_t* __restrict__ 
 // while the previous bin's queries are answered from the other buffer, so the
 // copies overlap the work.  Buckets longer than WALK_WARP keys go to the
 // long-bucket list as in the direct probe; a bin whose keys do not fit is
-// walked in global memory.  Every wait on a copy is bounded.
-constexpr uint32_t BIN_KEY_BYTES = 80 * 1024;                                  // per buffer
+// walked in global memory.  Equal query keys share a bucket, hence a bin: for
+// 32-bit keys, the count of every warp-walked bucket is kept in a small
+// per-bin shared-memory table, so a key queried again in the same bin is
+// answered without walking (the per-bucket list intersection of Sec. 3.3
+// matches each distinct query key once).  Every wait on a copy is bounded.
+constexpr uint32_t BIN_KEY_BYTES = 78 * 1024;                                  // per buffer
 constexpr uint32_t BIN_OFF_BYTES = ((BIN_BUCKETS + 1) * 4 + 15) / 16 * 16;     // 8193 offsets, rounded to 16 B
 constexpr uint32_t BIN_BUF_BYTES = BIN_OFF_BYTES + BIN_KEY_BYTES;
 constexpr int BIN_PROBE_THREADS = 1024;
 constexpr uint32_t COPY_WAIT_LIMIT = 1u << 26;  // polls of a copy's barrier (far beyond any real copy)
+constexpr uint32_t CACHE_SLOTS = 512;           // per-bin (key, count) table; linear probing
+constexpr uint32_t CACHE_PROBES = 8;
+constexpr unsigned long long CACHE_EMPTY = ~0ull;  // a count never reaches 2^32 - 1 here
 
 template <typename K, int OUT, bool TOTAL>
 __global__ void __launch_bounds__(BIN_PROBE_THREADS, 1)
@@ -561,6 +568,8 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_bin[2], s_k0[2], s_klo[2], s_staged[2];
+    constexpr bool CACHE = sizeof(K) == 4;
+    __shared__ unsigned long long s_cache[CACHE ? CACHE_SLOTS : 1];  // (count << 32 | key)
     const unsigned lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint64_t B = H.B;
@@ -600,6 +609,8 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
     bool failed = false;
     while (true) {
         if (threadIdx.x == 0) issue(cur ^ 1);  // the previous user of that buffer finished at the last barrier
+        if (CACHE)
+            for (uint32_t t = threadIdx.x; t < CACHE_SLOTS; t += blockDim.x) s_cache[t] = CACHE_EMPTY;
         __syncthreads();
         const uint32_t p = s_bin[cur];
         if (p >= nbins) break;
@@ -631,9 +642,9 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
                 const uint32_t inext = i + nwarps * 32;
                 key_next = inext < q1 ? __ldg(qs + inext) : (K)0;
             }
-            uint32_t lo = 0, hi = 0;
+            uint32_t lo = 0, hi = 0, j = 0;
             if (ok) {
-                uint32_t j = bucket_of(key, H) - (uint32_t)b0;
+                j = bucket_of(key, H) - (uint32_t)b0;
                 if (j >= nb) j = nb - 1;  // queries of this bin hash into it by construction
                 lo = min(s_off[j], n_keys) - k0;
                 hi = max(min(s_off[j + 1], n_keys) - k0, lo);
@@ -656,7 +667,22 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
                     else cls = CLS_WARP;
                 }
             }
+            // a key already walked in this bin takes its count from the table
+            if (CACHE && cls == CLS_WARP) {
+                uint32_t sl = j & (CACHE_SLOTS - 1);
+                for (uint32_t t = 0; t < CACHE_PROBES; ++t) {
+                    const unsigned long long w = s_cache[sl];
+                    if (w == CACHE_EMPTY) break;
+                    if ((uint32_t)w == (uint32_t)key) {
+                        cnt = (uint32_t)(w >> 32);
+                        cls = CLS_NONE;
+                        break;
+                    }
+                    sl = (sl + 1) & (CACHE_SLOTS - 1);
+                }
+            }
             unsigned mm = __ballot_sync(FULL_MASK, cls == CLS_WARP);
+            const bool walked = cls == CLS_WARP;
             while (mm) {
                 const int src = __ffs(mm) - 1;
                 mm &= mm - 1;
@@ -667,6 +693,15 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
                 for (uint32_t x = l + lane; x < h; x += 32) c += (kb[x] == kk);
                 c = __reduce_add_sync(FULL_MASK, c);
                 if ((int)lane == src) cnt = c;
+            }
+            if (CACHE && walked) {  // record the walk (a full neighbourhood just skips it)
+                const unsigned long long w = ((unsigned long long)cnt << 32) | (uint32_t)key;
+                uint32_t sl = j & (CACHE_SLOTS - 1);
+                for (uint32_t t = 0; t < CACHE_PROBES; ++t) {
+                    const unsigned long long old = atomicCAS(&s_cache[sl], CACHE_EMPTY, w);
+                    if (old == CACHE_EMPTY || (uint32_t)old == (uint32_t)key) break;
+                    sl = (sl + 1) & (CACHE_SLOTS - 1);
+                }
             }
             if (ok) {
                 if (OUT == OUT_U32) static_cast<uint32_t*>(counts)[i] = cnt;
