@@ -50,6 +50,22 @@ def workload_desc(log2n):
             f"murmur3-fmix32 seed 0, Q=2^{log2n} queries 70% hits (ranks uniform over the 2^24 values)")
 
 
+def max_over_ranks(values, dist, device):
+    """Elementwise maximum of per-rank timings (the slowest replica sets the
+    job's time); the identity when there is no process group."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def aggregate_gkeys(world, keys_per_rank, ms):
+    """Whole-job throughput: every replica processes keys_per_rank keys in ms."""
+    return world * keys_per_rank / (ms * 1e-3) / 1e9
+
+
 def make_workload(log2n, salt):
     import workloads as W
     return W.zipf_large(n=1 << log2n, num_buckets=1 << (log2n - 1), q=1 << log2n, M=1 << 24, hit=0.7, salt=salt)
@@ -283,12 +299,9 @@ def run_ours(args, rank, world, local_rank):
         time.sleep(0.2)
 
     # max over ranks
-    if dist is not None:
-        tt = torch.tensor([ms, e2e["ms"] if e2e else 0.0], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt[0])
-        if e2e:
-            e2e["ms"] = float(tt[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e["ms"] if e2e else 0.0], dist, dev)
+    if e2e:
+        e2e["ms"] = e2e_ms
 
     # sanity: the total equals the sum of counts of the last step
     ok_total = int(total.cpu().numpy().view(np.uint64)[0]) == int(counts.cpu().numpy().view(np.uint32).sum(dtype=np.uint64))
@@ -298,7 +311,7 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
-    value = world * (N + Q) / (ms * 1e-3) / 1e9
+    value = aggregate_gkeys(world, N + Q, ms)
     peak, peak_kind = measured_peak()
     # Algorithmic bytes per launch of each kernel (k = 4 key bytes, v = 0 value
     # bytes, o = 4 offset bytes; W = keys walked by all bucket walks, W_long =
@@ -358,7 +371,7 @@ def run_ours(args, rank, world, local_rank):
         "check": {"total_equals_sum_of_counts": ok_total},
     }
     if e2e:
-        line["e2e"] = {"value": world * (N + Q) / (e2e["ms"] * 1e-3) / 1e9, "unit": UNIT,
+        line["e2e"] = {"value": aggregate_gkeys(world, N + Q, e2e["ms"]), "unit": UNIT,
                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                        "ms_per_step": e2e["ms"]}
     if world == 1 and not args.no_cpu:
