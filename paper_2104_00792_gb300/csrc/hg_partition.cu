@@ -439,6 +439,8 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
     uint64_t lo, hi;
     chunk_range(cm, c, seg, first, lo, hi);
     const bool vec = (reinterpret_cast<uintptr_t>(in + lo) & 15) == 0;
+    // every tile starts G records after a multiple of G, so one check covers the chunk
+    const bool dr_vec = DR && (reinterpret_cast<uintptr_t>(dr_out + lo) & (G * 4 - 1)) == 0;
     for (uint32_t d = threadIdx.x; d < RADIX; d += blockDim.x) {
         s_cnt[d] = 0;
         s_run[d] = d < R ? chunk_base[(uint64_t)c * RADIX + d] : 0u;
@@ -491,7 +493,20 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
                     s_dst[pos] = dst;
                 }
                 if (PM) s_pay[pos] = v[j];
-                if (DR) dr_t[(threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G)] = dr[j];
+                if (DR && !(dr_vec && cnt_tile == (uint32_t)TILE))
+                    dr_t[(threadIdx.x + (j / G) * PASS_THREADS) * G + (j % G)] = dr[j];
+            }
+        }
+        if (DR && dr_vec && cnt_tile == (uint32_t)TILE) {
+            // a full tile with aligned records: each thread's G records per group are
+            // consecutive, so they go out in one vector store
+#pragma unroll
+            for (int jj = 0; jj < IPT / G; ++jj) {
+                uint32_t* d = dr_t + (threadIdx.x + jj * PASS_THREADS) * G;
+                if constexpr (G == 4)
+                    *reinterpret_cast<uint4*>(d) = make_uint4(dr[jj * 4], dr[jj * 4 + 1], dr[jj * 4 + 2], dr[jj * 4 + 3]);
+                else
+                    *reinterpret_cast<uint2*>(d) = make_uint2(dr[jj * 2], dr[jj * 2 + 1]);
             }
         }
         __syncthreads();
