@@ -786,19 +786,28 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
         __syncthreads();
 
         // Choose the largest threshold whose non-bypassed ("cold") keys fit the
-        // staging buffer.  Each warp scans a contiguous slice of buckets.
-        const uint32_t slice = BPB / NW;
-        const uint32_t lo = w * slice;
-        uint32_t cold[NTHR] = {0, 0, 0, 0, 0};
-        for (uint32_t j = lo + lane; j < lo + slice; j += 32) {
-            const uint32_t c = s_cnt[j];
+        // staging buffer.  Thread t owns the CPT consecutive buckets from t * CPT
+        // (so each warp a contiguous slice) and keeps their counts in registers.
+        constexpr int CPT = (int)(BPB / LOCAL_THREADS);
+        static_assert(CPT % 4 == 0 && 32 % CPT == 0, "bucket slice per thread");
+        const uint32_t jt = threadIdx.x * CPT;
+        auto cnt4 = [&](int u0) { return *reinterpret_cast<const uint4*>(s_cnt + jt + u0); };
+        {
+            uint32_t cold[NTHR] = {0, 0, 0, 0, 0};
 #pragma unroll
-            for (int q = 0; q < NTHR; ++q) cold[q] += c < THR[q] ? c : 0u;
-        }
+            for (int u0 = 0; u0 < CPT; u0 += 4) {
+                const uint4 x = cnt4(u0);
+                const uint32_t cv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-        for (int q = 0; q < NTHR; ++q) {
-            cold[q] = __reduce_add_sync(FULL_MASK, cold[q]);
-            if (lane == 0) s_red[q][w] = cold[q];
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int q = 0; q < NTHR; ++q) cold[q] += cv[u] < THR[q] ? cv[u] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < NTHR; ++q) {
+                const uint32_t wsum = __reduce_add_sync(FULL_MASK, cold[q]);
+                if (lane == 0) s_red[q][w] = wsum;
+            }
         }
         __syncthreads();
         int sel = -1;
@@ -813,39 +822,63 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
         }
         const bool stage = sel >= 0;
         const uint32_t thr = stage ? THR[sel] : 0u;
-        // per-warp prefixes of all keys (q = 0 is "everything") and of the cold keys
+        // per-warp prefixes of all keys (q = 0 is "everything") and of the cold keys,
+        // then this thread's, then serially over its buckets
         uint32_t pre_all = 0, pre_cold = 0;
         for (int x = 0; x < w; ++x) {
             pre_all += s_red[0][x];
             if (stage) pre_cold += s_red[sel][x];
         }
-        uint32_t run_all = pre_all, run_cold = pre_cold;
-        for (uint32_t j0 = lo; j0 < lo + slice; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            const uint32_t c = s_cnt[j];
-            const bool hot = !stage || c >= thr;
-            const uint32_t ia = warp_inclusive_scan(c);
-            const uint32_t cc = hot ? 0u : c;
-            const uint32_t ic = warp_inclusive_scan(cc);
-            const uint32_t start = (uint32_t)s0 + run_all + ia - c;
-            const uint32_t cstart = run_cold + ic - cc;
-            if (j < nb) offsets[b0 + j] = start;
-            if (!hot) {
-                s_cnt[j] = cstart;
-            } else {
-                s_cnt[j] = start;
-                if (stage && c) {
-                    atomicOr(&s_hot[j >> 5], 1u << (j & 31));
-                    const uint32_t h = atomicAdd(&s_nhot, 1u);
-                    if (h < MAX_HOT) {
-                        s_hot_cpos[h] = cstart;
-                        s_hot_len[h] = c;
+        uint32_t t_all = 0, t_cold = 0;
+#pragma unroll
+        for (int u0 = 0; u0 < CPT; u0 += 4) {
+            const uint4 x = cnt4(u0);
+            const uint32_t cv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                t_all += cv[u];
+                t_cold += (!stage || cv[u] >= thr) ? 0u : cv[u];
+            }
+        }
+        uint32_t run_all = (uint32_t)s0 + pre_all + warp_inclusive_scan(t_all) - t_all;
+        uint32_t run_cold = pre_cold + warp_inclusive_scan(t_cold) - t_cold;
+        uint32_t hotbits = 0;
+#pragma unroll
+        for (int u0 = 0; u0 < CPT; u0 += 4) {  // four buckets at a time: one vector store each
+            const uint4 x = cnt4(u0);
+            const uint32_t cv[4] = {x.x, x.y, x.z, x.w};
+            uint32_t st[4], cur[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t cu = cv[u];
+                const bool hot = !stage || cu >= thr;
+                st[u] = run_all;
+                run_all += cu;
+                if (!hot) {
+                    cur[u] = run_cold;  // staging cursor
+                    run_cold += cu;
+                } else {
+                    cur[u] = st[u];  // global cursor
+                    if (stage && cu) {
+                        hotbits |= 1u << (u0 + u);
+                        const uint32_t h = atomicAdd(&s_nhot, 1u);
+                        if (h < MAX_HOT) {
+                            s_hot_cpos[h] = run_cold;
+                            s_hot_len[h] = cu;
+                        }
                     }
                 }
             }
-            run_all += __shfl_sync(FULL_MASK, ia, 31);
-            run_cold += __shfl_sync(FULL_MASK, ic, 31);
+            *reinterpret_cast<uint4*>(s_cnt + jt + u0) = make_uint4(cur[0], cur[1], cur[2], cur[3]);
+            if (jt + u0 + 4 <= nb) {
+                *reinterpret_cast<uint4*>(offsets + b0 + jt + u0) = make_uint4(st[0], st[1], st[2], st[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (jt + u0 + u < nb) offsets[b0 + jt + u0 + u] = st[u];
+            }
         }
+        if (hotbits) atomicOr(&s_hot[jt >> 5], hotbits << (jt & 31));
         __syncthreads();
         const uint32_t nhot = s_nhot;
         const bool staged = stage && nhot <= MAX_HOT;
