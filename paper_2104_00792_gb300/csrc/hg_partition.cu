@@ -26,6 +26,7 @@
 // The result equals the direct build's (offsets bit-exact; the order inside
 // a bucket differs, which Algorithm 1 leaves free).
 #include <cstdint>
+#include <type_traits>
 
 #include "hg_device.cuh"
 
@@ -774,15 +775,23 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
         if (threadIdx.x == 0) s_nhot = 0;
         __syncthreads();
 
-        // pass 1: bucket histogram
-        block_for_range<K, false>(in, nullptr, s0, s1, [&](uint64_t, K k, uint32_t, unsigned m) {
-            uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
-            if (j >= nb) {
-                atomicOr(err, DEVERR_BOUNDS);
-                j = nb - 1;
-            }
-            smem_add1(s_cnt, j, m);
-        });
+        // pass 1: bucket histogram.  Only a bin too large for the staging buffer
+        // can hold a heavily duplicated key, so only there do warps check for
+        // a shared counter first.
+        const bool heavy = s1 - s0 > STAGE_CAP;
+        auto hist = [&](auto fast) {
+            block_for_range<K, false>(in, nullptr, s0, s1, [&](uint64_t, K k, uint32_t, unsigned m) {
+                uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+                if (j >= nb) {
+                    atomicOr(err, DEVERR_BOUNDS);
+                    j = nb - 1;
+                }
+                if (decltype(fast)::value) smem_add1(s_cnt, j, m);
+                else atomicAdd(s_cnt + j, 1u);
+            });
+        };
+        if (heavy) hist(std::true_type{});
+        else hist(std::false_type{});
         __syncthreads();
 
         // Choose the largest threshold whose non-bypassed ("cold") keys fit the
@@ -906,25 +915,40 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
         __syncthreads();
 
         // pass 2: place (bypassing buckets straight to global memory, the rest staged)
-        block_for_range<K, HV>(in, in_v, s0, s1, [&](uint64_t, K k, uint32_t v, unsigned m) {
-            uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
-            if (j >= nb) j = nb - 1;  // flagged in pass 1
-            const uint32_t pos = smem_inc(s_cnt, j, m);
-            const bool hot = !staged || ((s_hot[j >> 5] >> (j & 31)) & 1u);
-            if (!hot) {
+        if (staged && nhot == 0 && !heavy) {
+            // the common bin: every key is staged, counters are rarely shared
+            block_for_range<K, HV>(in, in_v, s0, s1, [&](uint64_t, K k, uint32_t v, unsigned) {
+                uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+                if (j >= nb) j = nb - 1;  // flagged in pass 1
+                const uint32_t pos = atomicAdd(s_cnt + j, 1u);
                 if (pos < STAGE_CAP) {
                     s_keys[pos] = k;
                     if (HV) s_pay[pos] = v;
                 } else {
                     atomicOr(err, DEVERR_BOUNDS);
                 }
-            } else if (pos < n) {
-                out[pos] = k;
-                if (HV) out_v[pos] = v;
-            } else {
-                atomicOr(err, DEVERR_BOUNDS);
-            }
-        });
+            });
+        } else {
+            block_for_range<K, HV>(in, in_v, s0, s1, [&](uint64_t, K k, uint32_t v, unsigned m) {
+                uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+                if (j >= nb) j = nb - 1;  // flagged in pass 1
+                const uint32_t pos = smem_inc(s_cnt, j, m);
+                const bool hot = !staged || ((s_hot[j >> 5] >> (j & 31)) & 1u);
+                if (!hot) {
+                    if (pos < STAGE_CAP) {
+                        s_keys[pos] = k;
+                        if (HV) s_pay[pos] = v;
+                    } else {
+                        atomicOr(err, DEVERR_BOUNDS);
+                    }
+                } else if (pos < n) {
+                    out[pos] = k;
+                    if (HV) out_v[pos] = v;
+                } else {
+                    atomicOr(err, DEVERR_BOUNDS);
+                }
+            });
+        }
         __syncthreads();
         // staged keys: compacted position c goes to s0 + c + (lengths of hot buckets at or before c)
         if (staged) {
