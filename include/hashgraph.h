@@ -184,6 +184,74 @@ hg_status hg_probe_stats(const hg_table* t, const void* d_queries, uint64_t q, u
 hg_status hg_build_noalloc(const hg_config* cfg, const void* d_keys, const void* d_values, uint64_t n,
                            uint32_t* d_offsets, void* d_keys_out, uint32_t* d_values_out, hg_stream_t s);
 
+/*
+ * Batches: many independent tables of 32-bit keys, built and probed together
+ * in one persistent kernel launch (captured once in a CUDA graph and
+ * replayed).  Each table t is an ordinary HashGraph: its keys are
+ * d_keys[key_offsets[t] .. key_offsets[t+1]), its bucket count num_buckets[t],
+ * its queries d_queries[query_offsets[t] .. query_offsets[t+1]), and
+ * count[i] = the multiplicity of query i among table t's keys (Sec. 3.3,
+ * duplicates included).  The hash and seed are those of hg_build.  One CTA
+ * builds and probes a table at a time: a table with at most 2^bin_shift
+ * buckets and fuse_keys keys entirely in shared memory (histogram, scan and
+ * scatter fused); a larger one after partitioning its keys and queries by
+ * bin (bucket >> bin_shift, the binning of Sec. 3.2).  The per-table offsets
+ * equal hg_build's; the order of keys inside a bucket is unspecified.
+ */
+typedef struct hg_batch hg_batch; /* opaque; owns the tables' CSR arrays and scratch */
+
+typedef struct {
+    uint32_t threads;   /* threads per CTA: 256 or 512 */
+    uint32_t bin_shift; /* log2 of buckets per bin: 12 or 13 */
+    uint32_t fuse_keys; /* tables with at most this many keys (and 2^bin_shift buckets) take the fused path */
+} hg_batch_params;
+
+/*
+ * hg_batch_create -- plan a batch and allocate its device arrays.
+ *   cfg            key_bytes = 4, value_bytes = 0, seed; num_buckets and flags are ignored
+ *   n_tables       >= 1
+ *   h_key_offsets  host, n_tables + 1 nondecreasing uint64_t from 0: table t's keys
+ *   h_num_buckets  host, n_tables values in [1, 2^21]
+ *   h_query_offsets host, n_tables + 1 nondecreasing uint64_t from 0, or NULL (no queries)
+ * Each table holds fewer than 2^32 keys and queries.  Copies the host arrays
+ * (synchronises `s` once).  Default parameters: 512 threads, bin_shift 13,
+ * fuse_keys 16384.
+ */
+hg_status hg_batch_create(const hg_config* cfg, uint32_t n_tables, const uint64_t* h_key_offsets,
+                          const uint64_t* h_num_buckets, const uint64_t* h_query_offsets, hg_stream_t s,
+                          hg_batch** out);
+
+/*
+ * hg_batch_run -- build every table from d_keys (concatenated as planned) and
+ * write d_counts[i] for every query of d_queries; one kernel launch.  The
+ * first run with given pointers and parameters captures a CUDA graph on `s`
+ * (unless `s` is the legacy default stream or is being captured by the
+ * caller, in which case the kernel is launched directly); later runs with the
+ * same pointers replay it.  The tables stay readable through hg_batch_view
+ * until the next run or hg_batch_free.
+ */
+hg_status hg_batch_run(hg_batch* b, const uint32_t* d_keys, const uint32_t* d_queries, uint32_t* d_counts,
+                       hg_stream_t s);
+
+/*
+ * hg_batch_tune -- autotuner: run the batch once per candidate parameter set
+ * (threads 256/512, bin_shift 12/13, fuse_keys 2^bin_shift or half of it),
+ * time each with CUDA events on `s`, keep the fastest (also returned in
+ * *chosen if not NULL).  Synchronises `s`; the outputs hold the last run's.
+ */
+hg_status hg_batch_tune(hg_batch* b, const uint32_t* d_keys, const uint32_t* d_queries, uint32_t* d_counts,
+                        hg_stream_t s, hg_batch_params* chosen);
+hg_status hg_batch_set_params(hg_batch* b, const hg_batch_params* p);
+hg_status hg_batch_get_params(const hg_batch* b, hg_batch_params* p);
+
+/* Borrow table t's CSR arrays: d_offsets (num_buckets + 1 uint32_t, relative to the table) and d_keys. */
+hg_status hg_batch_view(const hg_batch* b, uint32_t table, const void** d_offsets, const void** d_keys, uint64_t* n,
+                        uint64_t* num_buckets);
+/* Wait for `s`; HG_ERR_CUDA if a batch kernel recorded an out-of-range index. */
+hg_status hg_batch_sync(const hg_batch* b, hg_stream_t s);
+/* Stream-ordered free of every array the batch owns; NULL is accepted. */
+hg_status hg_batch_free(hg_batch* b, hg_stream_t s);
+
 /* Number of kernels this process has launched through the library so far. */
 uint64_t hg_launch_count(void);
 

@@ -231,3 +231,110 @@ def hg_prof_names() -> list[str]:
 
 def hg_version() -> str:
     return lib.hg_version().decode()
+
+
+# ---------------------------------------------------------------- batches --
+class hg_batch_params(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("bin_shift", ctypes.c_uint32), ("fuse_keys", ctypes.c_uint32)]
+
+
+lib.hg_batch_create.argtypes = [ctypes.POINTER(hg_config), ctypes.c_uint32, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]
+lib.hg_batch_run.argtypes = [_vp, _vp, _vp, _vp, _vp]
+lib.hg_batch_tune.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(hg_batch_params)]
+lib.hg_batch_set_params.argtypes = [_vp, ctypes.POINTER(hg_batch_params)]
+lib.hg_batch_get_params.argtypes = [_vp, ctypes.POINTER(hg_batch_params)]
+lib.hg_batch_view.argtypes = [_vp, ctypes.c_uint32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u64),
+                              ctypes.POINTER(_u64)]
+lib.hg_batch_sync.argtypes = [_vp, _vp]
+lib.hg_batch_free.argtypes = [_vp, _vp]
+for _f in ("hg_batch_create", "hg_batch_run", "hg_batch_tune", "hg_batch_set_params", "hg_batch_get_params",
+           "hg_batch_view", "hg_batch_sync", "hg_batch_free"):
+    getattr(lib, _f).restype = ctypes.c_int
+
+
+class Batch:
+    """Handle of a planned batch of tables (owns the library's hg_batch*)."""
+
+    def __init__(self, handle: int, n_tables: int, stream: int):
+        self.handle = handle
+        self.n_tables = n_tables
+        self._stream = stream
+
+    def free(self, stream=None):
+        if self.handle:
+            _check(lib.hg_batch_free(self.handle, _stream(stream) if stream is not None else self._stream))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _host_u64(values) -> "ctypes.Array":
+    vals = [int(x) for x in values]
+    return (ctypes.c_uint64 * len(vals))(*vals)
+
+
+def hg_batch_create(key_offsets, num_buckets, query_offsets=None, seed: int = 0, stream=None) -> Batch:
+    """Plan a batch: key_offsets / query_offsets are n_tables + 1 host integers, num_buckets n_tables."""
+    n_tables = len(num_buckets)
+    if len(key_offsets) != n_tables + 1 or (query_offsets is not None and len(query_offsets) != n_tables + 1):
+        raise ValueError("offsets need n_tables + 1 entries")
+    cfg = hg_config(4, 0, 1, seed, 0)
+    ko, nb = _host_u64(key_offsets), _host_u64(num_buckets)
+    qo = _host_u64(query_offsets) if query_offsets is not None else None
+    h = _vp()
+    s = _stream(stream)
+    _check(lib.hg_batch_create(ctypes.byref(cfg), n_tables, ctypes.cast(ko, _vp), ctypes.cast(nb, _vp),
+                               ctypes.cast(qo, _vp) if qo is not None else None, s, ctypes.byref(h)))
+    return Batch(h.value, n_tables, s)
+
+
+def hg_batch_run(batch: Batch, keys: torch.Tensor, queries: torch.Tensor | None, counts: torch.Tensor | None,
+                 stream=None):
+    """Build every table and count every query in one persistent launch."""
+    _check(lib.hg_batch_run(batch.handle, _ptr(keys), _ptr(queries), _ptr(counts), _stream(stream)))
+
+
+def hg_batch_tune(batch: Batch, keys: torch.Tensor, queries: torch.Tensor | None, counts: torch.Tensor | None,
+                  stream=None) -> dict:
+    """Time every candidate parameter set on this batch and keep the fastest."""
+    p = hg_batch_params()
+    _check(lib.hg_batch_tune(batch.handle, _ptr(keys), _ptr(queries), _ptr(counts), _stream(stream),
+                             ctypes.byref(p)))
+    return {"threads": p.threads, "bin_shift": p.bin_shift, "fuse_keys": p.fuse_keys}
+
+
+def hg_batch_set_params(batch: Batch, threads: int, bin_shift: int, fuse_keys: int):
+    p = hg_batch_params(threads, bin_shift, fuse_keys)
+    _check(lib.hg_batch_set_params(batch.handle, ctypes.byref(p)))
+
+
+def hg_batch_get_params(batch: Batch) -> dict:
+    p = hg_batch_params()
+    _check(lib.hg_batch_get_params(batch.handle, ctypes.byref(p)))
+    return {"threads": p.threads, "bin_shift": p.bin_shift, "fuse_keys": p.fuse_keys}
+
+
+def hg_batch_view(batch: Batch, table: int):
+    """(offsets, keys) of one table as zero-copy int32 CUDA tensors."""
+    o, k = _vp(), _vp()
+    n, B = _u64(), _u64()
+    _check(lib.hg_batch_view(batch.handle, table, ctypes.byref(o), ctypes.byref(k), ctypes.byref(n), ctypes.byref(B)))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    offs = torch.as_tensor(_DeviceArray(o.value, B.value + 1, "<i4"), device=dev)
+    keys = torch.as_tensor(_DeviceArray(k.value, n.value, "<i4"), device=dev) if n.value else \
+        torch.empty(0, dtype=torch.int32, device=dev)
+    return offs, keys
+
+
+def hg_batch_sync(batch: Batch, stream=None):
+    _check(lib.hg_batch_sync(batch.handle, _stream(stream)))

@@ -87,3 +87,19 @@ def test_join_probe_structure():
     frac = np.mean([k in keyset for k in singles.tolist()])
     assert abs(frac - 0.5) < 0.05
     assert wl.values.dtype == np.uint32 and wl.values.size == wl.keys.size
+
+
+def test_batched_uniform_recipe():
+    b = W.batched_uniform(200, 8, 20, salt=1)
+    sizes = np.diff(b.key_offsets.astype(np.int64))
+    assert sizes.min() >= 2 ** 8 and sizes.max() <= 2 ** 20
+    assert np.array_equal(b.num_buckets.astype(np.int64), sizes)          # B_t = N_t
+    assert np.array_equal(b.query_offsets, b.key_offsets)                  # N_t queries per table
+    # log-uniform: about half the tables fall below the geometric midpoint 2^14
+    assert 0.35 < np.mean(sizes < 2 ** 14) < 0.65
+    # deterministic, and each table's keys come from its own stream
+    again = W.batched_uniform(200, 8, 20, salt=1)
+    assert np.array_equal(again.keys, b.keys) and np.array_equal(again.queries, b.queries)
+    k0, _, _ = b.table(0)
+    k1, _, _ = b.table(1)
+    assert not np.array_equal(k0[:16], k1[:16])

@@ -21,6 +21,10 @@ Recipes (master seed ``MASTER_SEED``; stream ids in ``STREAM``):
   whose ``hot_frac`` share of slots holds ``rep`` copies each of hot keys;
   every distinct probe key is a build key with probability 1/2, else fresh;
   slots are Fisher-Yates shuffled.
+* ``batched_uniform`` -- many independent tables: table t has
+  N_t = round(2^(lo + (hi - lo) u_t)) keys (u_t uniform in [0, 1) from the
+  ``sizes`` stream, so sizes are log-uniform), B_t = N_t buckets, and N_t
+  queries, each table drawn like ``plain_uniform`` from its own streams.
 """
 from __future__ import annotations
 
@@ -42,6 +46,7 @@ STREAM = {
     "q_select": 3,
     "q_miss": 4,
     "shuffle": 5,
+    "sizes": 6,
 }
 
 _lib = None
@@ -201,3 +206,48 @@ def join_kv(n: int = 1 << 27, num_buckets: int = 1 << 26, q: int = 1 << 26, hot_
     _load().hgw_join_probe_u64(_ptr(keys), n, stream("q_select", master, salt), stream("q_miss", master, salt),
                                stream("shuffle", master, salt), q, hot, rep, _ptr(probe))
     return Workload("join_kv", keys, values, probe, num_buckets)
+
+
+@dataclass
+class BatchWorkload:
+    """Inputs of a batch of independent tables, concatenated table by table."""
+    name: str
+    keys: np.ndarray            # uint32, all tables' keys
+    key_offsets: np.ndarray     # uint64 [n_tables + 1]
+    num_buckets: np.ndarray     # uint64 [n_tables]
+    queries: np.ndarray         # uint32, all tables' queries
+    query_offsets: np.ndarray   # uint64 [n_tables + 1]
+    seed: int = 0
+
+    @property
+    def n_tables(self) -> int:
+        return int(self.num_buckets.size)
+
+    def table(self, t: int):
+        """(keys, num_buckets, queries) of table t (views)."""
+        k0, k1 = int(self.key_offsets[t]), int(self.key_offsets[t + 1])
+        q0, q1 = int(self.query_offsets[t]), int(self.query_offsets[t + 1])
+        return self.keys[k0:k1], int(self.num_buckets[t]), self.queries[q0:q1]
+
+
+def batch_sizes(n_tables: int, lo_log2: float, hi_log2: float, master: int = MASTER_SEED, salt: int = 0) -> np.ndarray:
+    """Log-uniform table sizes round(2^(lo + (hi - lo) u)), u = (draw >> 11) * 2^-53."""
+    st = stream("sizes", master, salt)
+    u = np.array([(splitmix64_at(st, t) >> 11) * 2.0 ** -53 for t in range(n_tables)], dtype=np.float64)
+    return np.rint(np.power(2.0, lo_log2 + (hi_log2 - lo_log2) * u)).astype(np.uint64)
+
+
+def batched_uniform(n_tables: int = 4096, lo_log2: float = 8, hi_log2: float = 20, hit: float = 0.5,
+                    master: int = MASTER_SEED, salt: int = 0) -> BatchWorkload:
+    sizes = batch_sizes(n_tables, lo_log2, hi_log2, master, salt)
+    ko = np.zeros(n_tables + 1, dtype=np.uint64)
+    ko[1:] = np.cumsum(sizes)
+    keys = np.empty(int(ko[-1]), dtype=np.uint32)
+    queries = np.empty(int(ko[-1]), dtype=np.uint32)
+    for t in range(n_tables):
+        tsalt = (salt << 16) + t + 1
+        k0, k1 = int(ko[t]), int(ko[t + 1])
+        keys[k0:k1] = uniform_u32(stream("keys", master, tsalt), k1 - k0)
+        queries[k0:k1] = probe_mix(keys[k0:k1], k1 - k0, hit, stream("q_select", master, tsalt),
+                                   stream("q_miss", master, tsalt))
+    return BatchWorkload("batched_uniform", keys, ko, sizes.copy(), queries, ko.copy())
