@@ -249,6 +249,12 @@ hg_status hg_batch_view(const hg_batch* b, uint32_t table, const void** d_offset
                         uint64_t* num_buckets);
 /* Wait for `s`; HG_ERR_CUDA if a batch kernel recorded an out-of-range index. */
 hg_status hg_batch_sync(const hg_batch* b, hg_stream_t s);
+/*
+ * Byte-model helper (diagnostics, not part of a run): d_stats[0] = the sum over
+ * every query of its bucket's length in the built tables (the keys its walk
+ * visits).  d_stats: 1 device uint64_t, overwritten.  Call after hg_batch_run.
+ */
+hg_status hg_batch_walk_stats(const hg_batch* b, const uint32_t* d_queries, uint64_t* d_stats, hg_stream_t s);
 /* Stream-ordered free of every array the batch owns; NULL is accepted. */
 hg_status hg_batch_free(hg_batch* b, hg_stream_t s);
 

@@ -246,9 +246,10 @@ lib.hg_batch_get_params.argtypes = [_vp, ctypes.POINTER(hg_batch_params)]
 lib.hg_batch_view.argtypes = [_vp, ctypes.c_uint32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u64),
                               ctypes.POINTER(_u64)]
 lib.hg_batch_sync.argtypes = [_vp, _vp]
+lib.hg_batch_walk_stats.argtypes = [_vp, _vp, _vp, _vp]
 lib.hg_batch_free.argtypes = [_vp, _vp]
 for _f in ("hg_batch_create", "hg_batch_run", "hg_batch_tune", "hg_batch_set_params", "hg_batch_get_params",
-           "hg_batch_view", "hg_batch_sync", "hg_batch_free"):
+           "hg_batch_view", "hg_batch_sync", "hg_batch_free", "hg_batch_walk_stats"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -338,3 +339,10 @@ def hg_batch_view(batch: Batch, table: int):
 
 def hg_batch_sync(batch: Batch, stream=None):
     _check(lib.hg_batch_sync(batch.handle, _stream(stream)))
+
+
+def hg_batch_walk_stats(batch: Batch, queries: torch.Tensor, stream=None) -> int:
+    """Sum of the queries' bucket lengths in the built tables (synchronises the stream)."""
+    st = torch.empty(1, dtype=torch.int64, device=queries.device)
+    _check(lib.hg_batch_walk_stats(batch.handle, _ptr(queries), _ptr(st), _stream(stream)))
+    return int(st.item())

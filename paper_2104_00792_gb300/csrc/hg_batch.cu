@@ -330,6 +330,25 @@ __global__ void __launch_bounds__(T, 2) k_batch(BatchArgs A) {
     }
 }
 
+// Byte-model helper: stats[0] += the bucket length of every query (the keys
+// its walk visits), from the built tables.  One CTA per table.
+__global__ void __launch_bounds__(256) k_batch_walk(const BatchTable* __restrict__ tabs, uint32_t n_tables,
+                                                    const uint32_t* __restrict__ offsets_out,
+                                                    const uint32_t* __restrict__ queries,
+                                                    unsigned long long* stats) {
+    uint64_t w = 0;
+    for (uint32_t t = blockIdx.x; t < n_tables; t += gridDim.x) {
+        const BatchTable tb = tabs[t];
+        const uint32_t* offs = offsets_out + tb.off_begin;
+        for (uint32_t i = threadIdx.x; i < tb.q; i += blockDim.x) {
+            const uint32_t j = bucket_of(queries[tb.q_begin + i], tb.H);
+            w += offs[j + 1] - offs[j];
+        }
+    }
+    const uint64_t tot = warp_sum(w);
+    if (lane_id() == 0 && tot) atomicAdd(stats, (unsigned long long)tot);
+}
+
 }  // namespace
 }  // namespace hg
 
@@ -442,11 +461,17 @@ cudaError_t run_graph(hg_batch* b, const uint32_t* keys, const uint32_t* queries
         if (e != cudaSuccess) return e;
         // the legacy default stream cannot be captured, and a stream the caller is
         // already capturing takes the launch into the caller's own graph
-        if (s == nullptr || s == cudaStreamLegacy) return enqueue_batch(b, p, keys, queries, counts, s);
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        e = cudaStreamIsCapturing(s, &cs);
-        if (e != cudaSuccess) return e;
-        if (cs != cudaStreamCaptureStatusNone) return enqueue_batch(b, p, keys, queries, counts, s);
+        if (s != nullptr && s != cudaStreamLegacy) {
+            e = cudaStreamIsCapturing(s, &cs);
+            if (e != cudaSuccess) return e;
+        }
+        if (s == nullptr || s == cudaStreamLegacy || cs != cudaStreamCaptureStatusNone) {
+            launch_begin("batch", s);
+            e = enqueue_batch(b, p, keys, queries, counts, s);
+            launch_end("batch", s);
+            return e;
+        }
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
         cudaError_t e2 = enqueue_batch(b, p, keys, queries, counts, s);
@@ -634,6 +659,22 @@ hg_status hg_batch_sync(const hg_batch* b, hg_stream_t st) {
     if (e != cudaSuccess) return bcuda(e, "hg_batch_sync");
     if (err) return bfail(HG_ERR_CUDA, "hg_batch_sync: a batch kernel found an index out of range");
     return HG_OK;
+}
+
+hg_status hg_batch_walk_stats(const hg_batch* b, const uint32_t* d_queries, uint64_t* d_stats, hg_stream_t st) {
+    if (!b || !d_stats || (b->total_q && !d_queries))
+        return bfail(HG_ERR_INVALID_ARG, "hg_batch_walk_stats: NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+    cudaError_t e = cudaMemsetAsync(d_stats, 0, sizeof(uint64_t), s);
+    if (e == cudaSuccess && b->total_q) {
+        const unsigned g = std::min<unsigned>(b->n_tables, (unsigned)num_sms() * 8);
+        launch_begin("walk_stats", s);
+        k_batch_walk<<<g, 256, 0, s>>>(b->d_tabs, b->n_tables, b->offsets_out, d_queries,
+                                       reinterpret_cast<unsigned long long*>(d_stats));
+        launch_end("walk_stats", s);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? HG_OK : bcuda(e, "hg_batch_walk_stats");
 }
 
 hg_status hg_batch_free(hg_batch* b, hg_stream_t st) {

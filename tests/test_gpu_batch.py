@@ -106,26 +106,57 @@ def test_batch_every_parameter_set(hg, params):
 
 
 def test_batch_tune_and_replay(hg):
+    # on a stream of its own the runs are captured once and replayed as a CUDA graph
     wl = W.batched_uniform(32, 4, 15, salt=10)
-    got, tables, chosen = _run(hg, wl, tune=True, runs=3)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        got, tables, chosen = _run(hg, wl, tune=True, runs=3)
+    torch.cuda.synchronize()
     assert (chosen["threads"], chosen["bin_shift"], chosen["fuse_keys"]) in PARAMS
     _check(wl, got, tables)
 
 
+def test_batch_graph_replays_count_one_launch_each(hg):
+    wl = W.batched_uniform(8, 4, 12, salt=13)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        keys, qs = to_dev(wl.keys), to_dev(wl.queries)
+        counts = torch.empty(wl.queries.size, dtype=torch.int32, device="cuda")
+        with hg.hg_batch_create(wl.key_offsets, wl.num_buckets, wl.query_offsets) as b:
+            hg.hg_batch_run(b, keys, qs, counts)
+            n0 = hg.hg_launch_count()
+            for _ in range(5):
+                hg.hg_batch_run(b, keys, qs, counts)
+            assert hg.hg_launch_count() - n0 == 5
+            hg.hg_batch_sync(b)
+            got = from_dev(counts, np.uint32)
+    for t in range(wl.n_tables):
+        k, B, q = wl.table(t)
+        q0, q1 = int(wl.query_offsets[t]), int(wl.query_offsets[t + 1])
+        want = oracle.build_table(np.ascontiguousarray(k), B, 0).query_count(np.ascontiguousarray(q))
+        assert np.array_equal(got[q0:q1].astype(np.uint64), want)
+
+
 def test_batch_replay_sees_new_inputs(hg):
     a = W.batched_uniform(16, 4, 14, salt=12)
-    keys, qs = to_dev(a.keys), to_dev(a.queries)
-    counts = torch.empty(a.queries.size, dtype=torch.int32, device="cuda")
-    with hg.hg_batch_create(a.key_offsets, a.num_buckets, a.query_offsets) as b:
-        hg.hg_batch_run(b, keys, qs, counts)
-        # same buffers, new contents: the replayed graph reads them
-        rng = np.random.default_rng(3)
-        new_q = a.queries.copy()
-        new_q[::3] = rng.integers(0, 1 << 32, size=new_q[::3].size, dtype=np.uint64).astype(np.uint32)
-        qs.copy_(to_dev(new_q))
-        hg.hg_batch_run(b, keys, qs, counts)
-        hg.hg_batch_sync(b)
-        got = from_dev(counts, np.uint32)
+    rng = np.random.default_rng(3)
+    new_q = a.queries.copy()
+    new_q[::3] = rng.integers(0, 1 << 32, size=new_q[::3].size, dtype=np.uint64).astype(np.uint32)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        keys, qs = to_dev(a.keys), to_dev(a.queries)
+        fresh = to_dev(new_q)
+        counts = torch.empty(a.queries.size, dtype=torch.int32, device="cuda")
+        with hg.hg_batch_create(a.key_offsets, a.num_buckets, a.query_offsets) as b:
+            hg.hg_batch_run(b, keys, qs, counts)
+            # same buffers, new contents: the replayed graph reads them
+            qs.copy_(fresh)
+            hg.hg_batch_run(b, keys, qs, counts)
+            hg.hg_batch_sync(b)
+            got = from_dev(counts, np.uint32)
     for t in range(a.n_tables):
         k, B, _ = a.table(t)
         q0, q1 = int(a.query_offsets[t]), int(a.query_offsets[t + 1])
@@ -143,3 +174,19 @@ def test_batch_rejects_bad_plans(hg):
     with hg.hg_batch_create([0, 4], [4], [0, 4]) as b:
         with pytest.raises(hg.HashGraphError):
             hg.hg_batch_set_params(b, 128, 13, 100)
+
+
+def test_batch_walk_stats(hg):
+    wl = W.batched_uniform(20, 4, 13, salt=14)
+    keys, qs = to_dev(wl.keys), to_dev(wl.queries)
+    counts = torch.empty(wl.queries.size, dtype=torch.int32, device="cuda")
+    with hg.hg_batch_create(wl.key_offsets, wl.num_buckets, wl.query_offsets) as b:
+        hg.hg_batch_run(b, keys, qs, counts)
+        w = hg.hg_batch_walk_stats(b, qs)
+    want = 0
+    for t in range(wl.n_tables):
+        k, B, q = wl.table(t)
+        ref = oracle.build_table(np.ascontiguousarray(k), B, 0)
+        lens = np.diff(ref.offsets.astype(np.int64))
+        want += int(lens[oracle.buckets(np.ascontiguousarray(q), B, 0)].sum())
+    assert w == want
