@@ -258,6 +258,52 @@ hg_status hg_batch_walk_stats(const hg_batch* b, const uint32_t* d_queries, uint
 /* Stream-ordered free of every array the batch owns; NULL is accepted. */
 hg_status hg_batch_free(hg_batch* b, hg_stream_t s);
 
+/*
+ * Serving: an engine that keeps tables of 32-bit keys resident under a
+ * device-memory budget and answers build and probe requests as they arrive
+ * (continuous batching).  The engine owns two streams (builds, probes).
+ * Residency is decided in arrival order: submitting a build makes its table
+ * resident (table bytes = hg_server_table_bytes(n, num_buckets)) and evicts
+ * the least recently used tables (a submitted probe marks its table used)
+ * until the resident bytes fit the budget; an evicted table's memory is
+ * released once the probes already queued for it have finished, and builds
+ * start in arrival order once the device holds room.  hg_server_poll()
+ * retires finished work, starts builds, and answers all queued probes whose
+ * tables exist with one coalesced launch (up to max_batch probes, over many
+ * tables; at most two such launches in flight), then reports completed
+ * requests.  A probe's counts equal hg_query_count's on the same table.
+ * Request buffers (keys, queries, counts) are borrowed until the request is
+ * reported complete.  Build scratch is transient and not counted in the
+ * budget.  Not thread-safe: call from one host thread.
+ */
+typedef struct hg_server hg_server;
+typedef struct {
+    uint64_t builds, probes, probe_launches, evictions; /* since creation */
+    uint64_t resident_tables, resident_bytes;           /* after the last poll */
+    uint64_t held_bytes;                                /* resident + evicted tables not yet released */
+    uint64_t pending, running;                          /* requests queued / launches in flight */
+} hg_server_stats_t;
+
+/* budget_bytes > 0; max_batch in [1, 256] probes per coalesced launch. */
+hg_status hg_server_create(uint64_t budget_bytes, uint32_t max_batch, hg_server** out);
+/* cfg: key_bytes 4, value_bytes 0, flags 0, 1 <= num_buckets <= 2^31.  table_id must not be in use.
+   HG_ERR_OOM if the table alone exceeds the budget.  *req_id identifies the request in hg_server_poll. */
+hg_status hg_server_submit_build(hg_server* s, uint64_t table_id, const hg_config* cfg, const void* d_keys,
+                                 uint64_t n, uint64_t* req_id);
+/* The table must be resident (built or queued, not evicted); d_counts: q uint32_t, written on completion. */
+hg_status hg_server_submit_probe(hg_server* s, uint64_t table_id, const void* d_queries, uint64_t q,
+                                 uint32_t* d_counts, uint64_t* req_id);
+/* Drive the engine; report up to max_done completed requests (ids and statuses; HG_OK on success). */
+hg_status hg_server_poll(hg_server* s, uint64_t* done_ids, int32_t* done_status, uint32_t max_done,
+                         uint32_t* n_done);
+hg_status hg_server_stats(const hg_server* s, hg_server_stats_t* out);
+/* Borrow a resident, dispatched table (for checks); valid until it is evicted and released. */
+hg_status hg_server_table(const hg_server* s, uint64_t table_id, hg_table** out);
+/* Device bytes the engine charges for a table of n keys and num_buckets buckets. */
+uint64_t hg_server_table_bytes(uint64_t n, uint64_t num_buckets);
+/* Wait for all work and free every table, stream and buffer of the engine; NULL is accepted. */
+hg_status hg_server_free(hg_server* s);
+
 /* Number of kernels this process has launched through the library so far. */
 uint64_t hg_launch_count(void);
 

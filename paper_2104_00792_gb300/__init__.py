@@ -100,15 +100,19 @@ _KEY_DTYPES = {torch.int32: 4, torch.uint32: 4, torch.int64: 8, torch.uint64: 8}
 class Table:
     """Handle of a device-resident HashGraph (owns the library's hg_table*)."""
 
-    def __init__(self, handle: int, key_bytes: int, n: int, num_buckets: int, has_values: bool, stream: int):
+    def __init__(self, handle: int, key_bytes: int, n: int, num_buckets: int, has_values: bool, stream: int,
+                 owned: bool = True):
         self.handle = handle
         self.key_bytes = key_bytes
         self.n = n
         self.num_buckets = num_buckets
         self.has_values = has_values
         self._stream = stream
+        self._owned = owned
 
     def free(self, stream=None):
+        if self.handle and not self._owned:  # borrowed (e.g. from a server): never freed here
+            self.handle = None
         if self.handle:
             _check(lib.hg_free(self.handle, _stream(stream) if stream is not None else self._stream))
             self.handle = None
@@ -346,3 +350,89 @@ def hg_batch_walk_stats(batch: Batch, queries: torch.Tensor, stream=None) -> int
     st = torch.empty(1, dtype=torch.int64, device=queries.device)
     _check(lib.hg_batch_walk_stats(batch.handle, _ptr(queries), _ptr(st), _stream(stream)))
     return int(st.item())
+
+
+# ---------------------------------------------------------------- serving --
+class hg_server_stats_t(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("builds", "probes", "probe_launches", "evictions", "resident_tables",
+                                               "resident_bytes", "held_bytes", "pending", "running")]
+
+
+lib.hg_server_create.argtypes = [_u64, ctypes.c_uint32, ctypes.POINTER(_vp)]
+lib.hg_server_submit_build.argtypes = [_vp, _u64, ctypes.POINTER(hg_config), _vp, _u64, ctypes.POINTER(_u64)]
+lib.hg_server_submit_probe.argtypes = [_vp, _u64, _vp, _u64, _vp, ctypes.POINTER(_u64)]
+lib.hg_server_poll.argtypes = [_vp, _vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+lib.hg_server_stats.argtypes = [_vp, ctypes.POINTER(hg_server_stats_t)]
+lib.hg_server_table.argtypes = [_vp, _u64, ctypes.POINTER(_vp)]
+lib.hg_server_table_bytes.argtypes = [_u64, _u64]
+lib.hg_server_table_bytes.restype = _u64
+lib.hg_server_free.argtypes = [_vp]
+for _f in ("hg_server_create", "hg_server_submit_build", "hg_server_submit_probe", "hg_server_poll",
+           "hg_server_stats", "hg_server_table", "hg_server_free"):
+    getattr(lib, _f).restype = ctypes.c_int
+
+
+def hg_server_table_bytes(n: int, num_buckets: int) -> int:
+    return lib.hg_server_table_bytes(n, num_buckets)
+
+
+class Server:
+    """The serving engine (owns the library's hg_server*).  Not thread-safe."""
+
+    def __init__(self, budget_bytes: int, max_batch: int = 256):
+        h = _vp()
+        _check(lib.hg_server_create(budget_bytes, max_batch, ctypes.byref(h)))
+        self.handle = h.value
+        self._ids = (ctypes.c_uint64 * 4096)()
+        self._st = (ctypes.c_int32 * 4096)()
+
+    def submit_build(self, table_id: int, keys: torch.Tensor, num_buckets: int, seed: int = 0) -> int:
+        cfg = hg_config(4, 0, num_buckets, seed, 0)
+        rid = _u64()
+        _check(lib.hg_server_submit_build(self.handle, table_id, ctypes.byref(cfg), _ptr(keys), keys.numel(),
+                                          ctypes.byref(rid)))
+        return rid.value
+
+    def submit_probe(self, table_id: int, queries: torch.Tensor, counts: torch.Tensor) -> int:
+        rid = _u64()
+        _check(lib.hg_server_submit_probe(self.handle, table_id, _ptr(queries), queries.numel(), _ptr(counts),
+                                          ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self) -> list:
+        """Drive the engine; (request id, status) of the requests that completed."""
+        n = ctypes.c_uint32()
+        _check(lib.hg_server_poll(self.handle, self._ids, self._st, 4096, ctypes.byref(n)))
+        return [(self._ids[i], self._st[i]) for i in range(n.value)]
+
+    def stats(self) -> dict:
+        st = hg_server_stats_t()
+        _check(lib.hg_server_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in hg_server_stats_t._fields_}
+
+    def table(self, table_id: int) -> Table:
+        """Borrow a resident table (for checks through hg_table_view)."""
+        h = _vp()
+        _check(lib.hg_server_table(self.handle, table_id, ctypes.byref(h)))
+        o, k, v = _vp(), _vp(), _vp()
+        n, B = _u64(), _u64()
+        _check(lib.hg_table_view(h.value, ctypes.byref(o), ctypes.byref(k), ctypes.byref(v), ctypes.byref(n),
+                                 ctypes.byref(B)))
+        return Table(h.value, 4, n.value, B.value, False, 0, owned=False)
+
+    def free(self):
+        if self.handle:
+            _check(lib.hg_server_free(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

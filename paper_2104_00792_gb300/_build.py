@@ -17,7 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libhashgraph.so")
 OBJDIR = os.path.join(HERE, "_build")
 
-SOURCES = ["hg_api.cu", "hg_scan.cu", "hg_build.cu", "hg_partition.cu", "hg_probe.cu", "hg_noalloc.cu", "hg_batch.cu"]
+SOURCES = ["hg_api.cu", "hg_scan.cu", "hg_build.cu", "hg_partition.cu", "hg_probe.cu", "hg_noalloc.cu", "hg_batch.cu",
+           "hg_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -38,6 +38,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "hg_workloads.c")
 LIB = os.path.join(HERE, "libhg_workloads.so")
+GPU_SRC = os.path.join(HERE, "hg_workloads_gpu.cu")
+GPU_LIB = os.path.join(HERE, "libhg_workloads_gpu.so")
 
 MASTER_SEED = 0x210400792
 STREAM = {
@@ -62,6 +64,48 @@ def build(force: bool = False) -> str:
         ])
         os.replace(tmp, LIB)
     return LIB
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile the device-side generators with nvcc (sm_103a)."""
+    if force or not os.path.exists(GPU_LIB) or os.path.getmtime(GPU_LIB) < os.path.getmtime(GPU_SRC):
+        tmp = GPU_LIB + ".tmp"
+        nvcc = os.environ.get("NVCC") or "nvcc"
+        if not os.path.exists(nvcc) and os.path.exists("/usr/local/cuda/bin/nvcc"):
+            nvcc = "/usr/local/cuda/bin/nvcc"
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC",
+                               "-shared", "-cudart", "static", "-o", tmp, GPU_SRC])
+        os.replace(tmp, GPU_LIB)
+    return GPU_LIB
+
+
+_gpu_lib = None
+
+
+def _load_gpu():
+    global _gpu_lib
+    if _gpu_lib is None:
+        build_gpu()
+        L = ctypes.CDLL(GPU_LIB)
+        u64, vp = ctypes.c_uint64, ctypes.c_void_p
+        L.hgw_gpu_uniform_u32.argtypes = [u64, u64, vp, vp]
+        L.hgw_gpu_probe_mix_uniform_u32.argtypes = [u64, u64, u64, u64, u64, u64, vp, vp]
+        _gpu_lib = L
+    return _gpu_lib
+
+
+def gpu_uniform_u32(state: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    """Device copy of uniform_u32 written to the device pointer out_ptr (n elements)."""
+    if _load_gpu().hgw_gpu_uniform_u32(state, n, out_ptr, stream) != 0:
+        raise RuntimeError("hgw_gpu_uniform_u32 launch failed")
+
+
+def gpu_probe_mix_uniform_u32(key_state: int, n_keys: int, q: int, hit: float, sel: int, miss: int, out_ptr: int,
+                              stream: int = 0) -> None:
+    """Device copy of probe_mix(uniform_u32(key_state, n_keys), q, hit, sel, miss)."""
+    if _load_gpu().hgw_gpu_probe_mix_uniform_u32(key_state, n_keys, sel, miss, hit_threshold(hit), q, out_ptr,
+                                                 stream) != 0:
+        raise RuntimeError("hgw_gpu_probe_mix_uniform_u32 launch failed")
 
 
 def _load():
@@ -251,3 +295,87 @@ def batched_uniform(n_tables: int = 4096, lo_log2: float = 8, hi_log2: float = 2
         queries[k0:k1] = probe_mix(keys[k0:k1], k1 - k0, hit, stream("q_select", master, tsalt),
                                    stream("q_miss", master, tsalt))
     return BatchWorkload("batched_uniform", keys, ko, sizes.copy(), queries, ko.copy())
+
+
+# ---------------------------------------------------------------- serving --
+def served_table_bytes(n: int, num_buckets: int) -> int:
+    """Device bytes a serving engine charges for a table (its keys, offsets and
+    a little padding); the same accounting as the engine's."""
+    return 4 * n + 4 * (num_buckets + 1) + 32
+
+
+@dataclass
+class ServeRequest:
+    kind: str          # "build" or "probe"
+    table: int         # table id (builds: the new table; probes: the target)
+    size: int          # keys of a build, queries of a probe
+    key_state: int     # the target table's key stream (uniform_u32)
+    sel: int = 0       # probes: hit selection and miss streams (probe_mix)
+    miss: int = 0
+    gap: float = 0.0   # exponential(1) inter-arrival gap before this request
+
+
+def serving_trace(n_requests: int = 200_000, build_frac: float = 0.3, build_log2=(10, 24), probe_log2=(8, 22),
+                  hit: float = 0.6, budget_bytes: int = 100 * 10**9, master: int = MASTER_SEED,
+                  salt: int = 0) -> list:
+    """Request stream of the serving workload.  Each request is a build with
+    probability build_frac (N log-uniform over 2^build_log2, B = N, keys
+    uniform_u32 from the table's own stream) or else a probe (Q log-uniform
+    over 2^probe_log2, hit fraction `hit` drawn from the target's keys) whose
+    target is uniform over the tables resident at that point under an
+    arrival-order LRU with the given budget (a build inserts its table and
+    evicts least recently used ones until the budget holds; a probe marks its
+    target used).  The first request is a build.  Gaps are exponential(1):
+    divide by the arrival rate for Poisson arrivals."""
+    from collections import OrderedDict
+    st_kind = stream("sizes", master, (salt << 16) + 0xFFFF)
+    out = []
+    resident: "OrderedDict[int, int]" = OrderedDict()   # table -> bytes, LRU first
+    res_list: list = []                                  # resident tables, for uniform picks
+    pos: dict = {}                                       # table -> index in res_list
+    info = {}                                            # table -> (n, key_state)
+    used = 0
+    next_table = 0
+    for r in range(n_requests):
+        x = splitmix64_at(st_kind, 3 * r)
+        y = splitmix64_at(st_kind, 3 * r + 1)
+        z = splitmix64_at(st_kind, 3 * r + 2)
+        u_kind = (x >> 11) * 2.0 ** -53
+        u_size = (y >> 11) * 2.0 ** -53
+        gap = -np.log1p(-((z >> 11) * 2.0 ** -53))
+        is_build = (r == 0) or not resident or u_kind < build_frac
+        if is_build:
+            lo, hi = build_log2
+            n = int(round(2.0 ** (lo + (hi - lo) * u_size)))
+            t = next_table
+            next_table += 1
+            ks = stream("keys", master, (salt << 24) + t + 1)
+            need = served_table_bytes(n, n)
+            while used + need > budget_bytes and resident:
+                old_t, b = resident.popitem(last=False)
+                used -= b
+                i = pos.pop(old_t)
+                last = res_list.pop()
+                if last != old_t:
+                    res_list[i] = last
+                    pos[last] = i
+            resident[t] = need
+            pos[t] = len(res_list)
+            res_list.append(t)
+            used += need
+            info[t] = (n, ks)
+            out.append(ServeRequest("build", t, n, ks, gap=gap))
+        else:
+            lo, hi = probe_log2
+            q = int(round(2.0 ** (lo + (hi - lo) * u_size)))
+            t = res_list[(x & 0xFFFFFFFF) * len(res_list) >> 32]
+            resident.move_to_end(t)
+            n, ks = info[t]
+            out.append(ServeRequest("probe", t, q, ks, sel=stream("q_select", master, (salt << 24) + (1 << 23) + r),
+                                    miss=stream("q_miss", master, (salt << 24) + (1 << 23) + r), gap=gap))
+    return out
+
+
+def serve_table_n(trace: list) -> dict:
+    """table id -> number of keys, from the trace's builds."""
+    return {r.table: r.size for r in trace if r.kind == "build"}
