@@ -42,8 +42,12 @@ def parse():
     p.add_argument("--cpu-sample-log2", type=int, default=27)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="zipf_large", choices=["zipf_large", "batched"],
-                   help="zipf_large: the 2^28 build+probe step; batched: 4096 tables in one persistent launch")
+    p.add_argument("--workload", default="zipf_large", choices=["zipf_large", "batched", "serving"],
+                   help="zipf_large: the 2^28 build+probe step; batched: 4096 tables in one persistent launch; "
+                        "serving: a Poisson stream of build and probe requests through the serving engine")
+    p.add_argument("--requests", type=int, default=200_000, help="serving: requests in the stream")
+    p.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / the plain path's capacity")
+    p.add_argument("--budget-gb", type=float, default=100.0, help="serving: device-memory budget for tables")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
     p.add_argument("--no-plain", action="store_true", help="batched: skip the one-launch-per-table comparison")
     return p.parse_args()
@@ -520,6 +524,157 @@ def run_batched(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+SERVE_METRIC = "served p99 latency ms (build+probe request stream)"
+
+
+def serve_desc(n, load, budget_gb):
+    return (f"serving: {n} requests, Poisson arrivals at {load:g} x the plain path's measured capacity; 30% builds "
+            f"(N log-uniform in [2^10, 2^24] uint32 keys, B = N), 70% probes (Q log-uniform in [2^8, 2^22], 60% hits "
+            f"from the target's keys) on tables resident under an arrival-order LRU with a {budget_gb:g} GB budget")
+
+
+def run_serving(args, rank, world, local_rank):
+    """Config: a request stream served by the engine, against one request at a time."""
+    import numpy as np
+    import torch
+
+    import paper_2104_00792_gb300 as hg
+    import workloads as W
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if rank != 0:  # one GPU per stream; replicas would serve independent streams
+        return
+    budget = int(args.budget_gb * 1e9)
+    trace = W.serving_trace(args.requests, budget_bytes=budget, salt=rank)
+    n_of = W.serve_table_n(trace)
+    nreq = len(trace)
+    stream = torch.cuda.current_stream(dev)
+    sid = stream.cuda_stream
+    gaps = np.array([r.gap for r in trace], dtype=np.float64)
+
+    def make_inputs(r):
+        if r.kind == "build":
+            k = torch.empty(max(r.size, 1), dtype=torch.int32, device=dev)
+            W.gpu_uniform_u32(r.key_state, r.size, k.data_ptr(), sid)
+            return k[: r.size], None
+        q = torch.empty(max(r.size, 1), dtype=torch.int32, device=dev)
+        W.gpu_probe_mix_uniform_u32(r.key_state, n_of[r.table], r.size, 0.6, r.sel, r.miss, q.data_ptr(), sid)
+        c = torch.empty(max(r.size, 1), dtype=torch.int32, device=dev)
+        return q[: r.size], c[: r.size]
+
+    sample = {i for i in range(nreq) if trace[i].kind == "probe" and i % 97 == 0}
+
+    def plain_run(arrivals, limit=None):
+        """One request at a time on one stream, tables kept under the same LRU."""
+        from collections import OrderedDict
+        tables = OrderedDict()
+        used = 0
+        done = np.zeros(nreq)
+        keep = {}
+        m = nreq if limit is None else limit
+        t0 = time.perf_counter()
+        for i in range(m):
+            r = trace[i]
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[i]:
+                    pass
+            a, c = make_inputs(r)
+            if r.kind == "build":
+                need = hg.hg_server_table_bytes(r.size, r.size)
+                while used + need > budget and tables:
+                    _, (tb, b) = tables.popitem(last=False)
+                    tb.free(stream)
+                    used -= b
+                tables[r.table] = (hg.hg_build(a, r.size, 0, stream=stream), need)
+                used += need
+            else:
+                tables.move_to_end(r.table)
+                hg.hg_query_count(tables[r.table][0], a, c, None, stream=stream)
+            stream.synchronize()
+            done[i] = time.perf_counter() - t0
+            if i in sample:
+                keep[i] = c.clone()
+        for tb, _ in tables.values():
+            tb.free(stream)
+        torch.cuda.synchronize(dev)
+        return done[:m], keep
+
+    def engine_run(arrivals, window=None):
+        """Requests submitted at their arrival times (or, with `window`, as soon
+        as fewer than `window` are outstanding: the engine's capacity)."""
+        srv = hg.Server(budget, max_batch=256)
+        done = np.zeros(nreq)
+        keep = {}
+        live = {}
+        i = 0
+        t0 = time.perf_counter()
+        while i < nreq or live:
+            now = time.perf_counter() - t0
+            while i < nreq and (arrivals[i] <= now if window is None else len(live) < window):
+                r = trace[i]
+                a, c = make_inputs(r)
+                stream.synchronize()  # the request arrives with its data in device memory
+                if r.kind == "build":
+                    rid = srv.submit_build(r.table, a, r.size)
+                else:
+                    rid = srv.submit_probe(r.table, a, c)
+                live[rid] = (i, a, c)
+                i += 1
+                now = time.perf_counter() - t0
+            for rid, st in srv.poll():
+                j, a, c = live.pop(rid)
+                done[j] = time.perf_counter() - t0
+                if st != hg.HG_OK:
+                    raise RuntimeError(f"request {j} failed with status {st}")
+                if j in sample:
+                    keep[j] = c
+        stats = srv.stats()
+        srv.free()
+        torch.cuda.synchronize(dev)
+        return done, keep, stats
+
+    # capacity of the plain path: its mean service time over the first requests, back to back
+    n_cal = min(nreq, 3000)
+    cal_done, _ = plain_run(None, limit=n_cal)
+    service = float(cal_done[-1]) / n_cal
+    rate = args.load / service
+    arrivals = np.cumsum(gaps) / rate
+    arrivals -= arrivals[0]
+    e_done, e_keep, e_stats = engine_run(arrivals)
+    p_done, p_keep = plain_run(arrivals)
+    same = all(torch.equal(e_keep[i], p_keep[i]) for i in sample)
+    keys_total = sum(r.size for r in trace)
+    # capacity: every request available at once (the engine keeps 64 outstanding)
+    cap_e, _, _ = engine_run(np.zeros(nreq), window=64)
+    cap_p, _ = plain_run(None)
+    capacity = {"engine_gkeys_per_s": keys_total / float(cap_e.max()) / 1e9,
+                "plain_gkeys_per_s": keys_total / float(cap_p.max()) / 1e9}
+    capacity["ratio"] = capacity["engine_gkeys_per_s"] / capacity["plain_gkeys_per_s"]
+
+    def summary(done):
+        lat = (done - arrivals) * 1e3
+        span = float(done.max())
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "gkeys_per_s": keys_total / span / 1e9, "makespan_s": span}
+
+    eng, pla = summary(e_done), summary(p_done)
+    line = {
+        "metric": SERVE_METRIC, "value": eng["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": nreq, "warmup": n_cal,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": serve_desc(nreq, args.load, args.budget_gb), "rate_per_s": rate,
+                   "plain_service_ms": service * 1e3},
+        "engine": eng, "plain": pla,
+        "vs_plain": {"p50": pla["p50_ms"] / eng["p50_ms"], "p99": pla["p99_ms"] / eng["p99_ms"],
+                     "throughput": eng["gkeys_per_s"] / pla["gkeys_per_s"]},
+        "capacity": capacity,
+        "engine_stats": e_stats,
+        "check": {"sampled_probes": len(sample), "engine_equals_plain": bool(same)},
+        "gpu_launches": int(e_stats["builds"] + e_stats["probe_launches"]),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -529,6 +684,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batched":
         run_batched(args, rank, world, local_rank)
+    elif args.workload == "serving":
+        run_serving(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
