@@ -46,6 +46,9 @@ def parse():
                    help="zipf_large: the 2^28 build+probe step; batched: 4096 tables in one persistent launch; "
                         "serving: a Poisson stream of build and probe requests through the serving engine")
     p.add_argument("--requests", type=int, default=200_000, help="serving: requests in the stream")
+    p.add_argument("--query-form", default="probe", choices=["probe", "intersect"],
+                   help="zipf_large: hg_query_count (grouped probe) or hg_query_count_intersect (HG(Q) + "
+                        "bucket intersections, the paper's query form)")
     p.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / the plain path's capacity")
     p.add_argument("--budget-gb", type=float, default=100.0, help="serving: device-memory budget for tables")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
@@ -242,9 +245,11 @@ def run_ours(args, rank, world, local_rank):
     total = torch.empty(1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    query = hg.hg_query_count_intersect if args.query_form == "intersect" else hg.hg_query_count
+
     def step():
         t = hg.hg_build(keys, B, 0, stream=stream)
-        hg.hg_query_count(t, queries, counts, total, stream=stream)
+        query(t, queries, counts, total, stream=stream)
         t.free(stream)
 
     for _ in range(max(args.warmup, 3)):
@@ -367,7 +372,9 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": workload_desc(args.log2n), "parallelism": f"replicas{world}",
                    "l2": "inputs exceed L2 (2 GiB read per step); no flush",
-                   "step": "hg_build + hg_query_count(counts, total) + hg_free"},
+                   "step": ("hg_build + hg_query_count_intersect(counts, total) + hg_free"
+                            if args.query_form == "intersect" else
+                            "hg_build + hg_query_count(counts, total) + hg_free")},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(dom), "peak_kind": peak_kind,
                      "step_model_bytes": step_bytes,

@@ -119,6 +119,18 @@ hg_status hg_query_gather(const hg_table* t, const void* d_queries, uint64_t q, 
                           uint32_t* d_out_values, uint64_t out_capacity, uint64_t* h_total, hg_stream_t s);
 
 /*
+ * hg_query_count_intersect -- the same per-slot counts (and total) as
+ * hg_query_count, computed by the paper's query form (Sec. 3.3): build
+ * HG(Q), a HashGraph of the queries with the table's num_buckets and seed
+ * whose values are the query slots, intersect bucket i of the table with
+ * bucket i of HG(Q) for every i (each query of HG(Q), taken in bucket order,
+ * walks its bucket of the table), and write each count to its slot.  q < 2^32.
+ * Allocates HG(Q) and its scratch on `s` and frees them before returning.
+ */
+hg_status hg_query_count_intersect(const hg_table* t, const void* d_queries, uint64_t q, uint32_t* d_counts,
+                                   uint64_t* d_total, hg_stream_t s);
+
+/*
  * hg_join_count -- *d_total = sum over query slots of their counts, i.e. the
  * inner-join cardinality of the table's keys with the queries.  d_total is one
  * device uint64_t, overwritten (not accumulated).

@@ -52,6 +52,8 @@ lib.hg_build.argtypes = [ctypes.POINTER(hg_config), _vp, _vp, _u64, _vp, ctypes.
 lib.hg_query_count.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp]
 lib.hg_query_gather.argtypes = [_vp, _vp, _u64, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]
 lib.hg_join_count.argtypes = [_vp, _vp, _u64, _vp, _vp]
+lib.hg_query_count_intersect.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp]
+lib.hg_query_count_intersect.restype = ctypes.c_int
 lib.hg_free.argtypes = [_vp, _vp]
 lib.hg_sync.argtypes = [_vp, _vp]
 lib.hg_table_view.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -150,6 +152,14 @@ def hg_query_count(table: Table, queries: torch.Tensor, counts: torch.Tensor | N
     """hg_query_count: per-slot multiplicities into `counts` (uint32/int32) and/or their sum into `total`."""
     _check(lib.hg_query_count(table.handle, _ptr(queries), queries.numel(), _ptr(counts), _ptr(total),
                               _stream(stream)))
+    return counts, total
+
+
+def hg_query_count_intersect(table: Table, queries: torch.Tensor, counts: torch.Tensor | None = None,
+                             total: torch.Tensor | None = None, stream=None):
+    """hg_query_count_intersect: the same counts by the paper's query form (HG(Q), then bucket intersections)."""
+    _check(lib.hg_query_count_intersect(table.handle, _ptr(queries), queries.numel(), _ptr(counts), _ptr(total),
+                                        _stream(stream)))
     return counts, total
 
 

@@ -42,7 +42,7 @@ std::atomic<uint64_t> g_launches{0};
 // ---- per-kernel event timing (diagnostics) ----
 const char* const kKernelNames[] = {"hist", "scan", "scatter", "probe", "long_prep", "long", "gather",
                                     "long_gather", "walk_stats", "part_hist", "part_plan", "chunk_scan", "chunk_count", "part_scatter", "huge_count",
-                                    "huge_scan", "bin_build", "q_part_count", "q_partition", "q_reverse", "batch", "probe_multi"};
+                                    "huge_scan", "bin_build", "q_part_count", "q_partition", "q_reverse", "batch", "probe_multi", "scatter_counts"};
 struct ProfRecord {
     const char* name;
     cudaEvent_t start, stop;
@@ -259,6 +259,22 @@ hg_status hg_query_count(const hg_table* ht, const void* d_queries, uint64_t q, 
     if ((st = check_device(t)) != HG_OK) return st;
     cudaError_t e = probe_count(*t, d_queries, q, d_counts, d_total, reinterpret_cast<cudaStream_t>(s));
     if (e != cudaSuccess) return cuda_fail(e, "hg_query_count");
+    return HG_OK;
+}
+
+hg_status hg_query_count_intersect(const hg_table* ht, const void* d_queries, uint64_t q, uint32_t* d_counts,
+                                   uint64_t* d_total, hg_stream_t s) {
+    const Table* t = reinterpret_cast<const Table*>(ht);
+    if (!t) return fail(HG_ERR_INVALID_ARG, "table is NULL");
+    if (!d_counts && !d_total && q > 0) return fail(HG_ERR_INVALID_ARG, "d_counts and d_total are both NULL");
+    if (d_counts && q > 0 && !aligned(d_counts, 4)) return fail(HG_ERR_INVALID_ARG, "d_counts is not 4-byte aligned");
+    if (d_total && !aligned(d_total, 8)) return fail(HG_ERR_INVALID_ARG, "d_total is not 8-byte aligned");
+    if (q >= (1ull << 32)) return fail(HG_ERR_INVALID_ARG, "q = %llu must be < 2^32", (unsigned long long)q);
+    hg_status st = check_queries(t, d_queries, q);
+    if (st != HG_OK) return st;
+    if ((st = check_device(t)) != HG_OK) return st;
+    cudaError_t e = count_by_intersection(*t, d_queries, q, d_counts, d_total, reinterpret_cast<cudaStream_t>(s));
+    if (e != cudaSuccess) return cuda_fail(e, "hg_query_count_intersect");
     return HG_OK;
 }
 

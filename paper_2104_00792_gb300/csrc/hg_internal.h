@@ -116,6 +116,11 @@ cudaError_t gather_values(const Table& t, const void* d_q, uint64_t q, const uin
                           uint32_t* out_values, GatherCtx* ctx, cudaStream_t s);
 void gather_release(GatherCtx* ctx, cudaStream_t s);
 
+// The paper's query form: HG(Q) built with the table's buckets and seed, then
+// bucket-by-bucket intersection with the table; per-slot counts as probe_count.
+cudaError_t count_by_intersection(const Table& t, const void* d_q, uint64_t q, uint32_t* counts, uint64_t* total,
+                                  cudaStream_t s);
+
 // Byte-model helper behind hg_probe_stats.
 cudaError_t probe_stats(const Table& t, const void* d_q, uint64_t q, uint64_t* stats, cudaStream_t s);
 

@@ -807,7 +807,79 @@ cudaError_t count_impl(const Table& t, const K* qs, uint64_t q, uint32_t* counts
     return e;
 }
 
+// counts[slot[j]] = src[j]: per-slot counts from counts in HG(Q) order.
+__global__ void __launch_bounds__(256) k_scatter_counts(const uint32_t* __restrict__ src,
+                                                        const uint32_t* __restrict__ slot, uint64_t q,
+                                                        uint32_t* __restrict__ dst) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < q; j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t sl = slot[j];
+        if (sl < q) dst[sl] = src[j];
+    }
+}
+
+// The paper's query form (Sec. 3.3): build HG(Q) over the queries with the
+// table's bucket count and seed, each query carrying its slot as its value;
+// then intersect bucket i of HG(A) with bucket i of HG(Q) for every i -- here
+// by walking, for each query of HG(Q) in bucket order, its bucket of the
+// table, so the table is read in bucket order -- and finally put the counts
+// back in slot order.
+template <typename K>
+cudaError_t intersect_impl(const Table& t, const K* qs, uint64_t q, uint32_t* counts, uint64_t* total,
+                           cudaStream_t s) {
+    Table qt;
+    qt.key_bytes = t.key_bytes;
+    qt.has_values = 1;
+    qt.flags = HG_INDEX_VALUES;
+    qt.device = t.device;
+    qt.n = q;
+    qt.B = t.B;
+    qt.seed = t.seed;
+    qt.H = t.H;
+    qt.err = t.err;
+    void* mem = nullptr;
+    LongList L{};
+    uint32_t* tmp = nullptr;
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&qt.offsets), (qt.B + 1) * sizeof(uint32_t) + 16, s);
+    if (e == cudaSuccess) e = dev_alloc(&qt.keys, q * sizeof(K) + 16, s);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void**>(&qt.values), q * 4, s);
+    if (e == cudaSuccess && counts) e = dev_alloc(reinterpret_cast<void**>(&tmp), q * 4 + 16, s);
+    if (e == cudaSuccess) {
+        const uint32_t cap = (uint32_t)(q < COUNT_LONG_CAP ? q : COUNT_LONG_CAP);
+        e = alloc_list(cap, false, s, &mem, &L);
+    }
+    if (e == cudaSuccess) e = build_table(qt, qs, nullptr, s);
+    const K* grouped = static_cast<const K*>(qt.keys);
+    if (e == cudaSuccess) {
+        if (counts && total) e = run_probe<K, OUT_U32, true, false>(t, grouped, q, tmp, total, L, nullptr, nullptr, s);
+        else if (counts) e = run_probe<K, OUT_U32, false, false>(t, grouped, q, tmp, nullptr, L, nullptr, nullptr, s);
+        else e = run_probe<K, OUT_NONE, true, false>(t, grouped, q, nullptr, total, L, nullptr, nullptr, s);
+    }
+    if (e == cudaSuccess && counts) {
+        launch_begin("scatter_counts", s);
+        k_scatter_counts<<<num_sms() * 8, 256, 0, s>>>(tmp, qt.values, q, counts);
+        launch_end("scatter_counts", s);
+        e = cudaGetLastError();
+    }
+    if (mem) dev_free(mem, s);
+    if (tmp) dev_free(tmp, s);
+    if (qt.values) dev_free(qt.values, s);
+    if (qt.keys) dev_free(qt.keys, s);
+    if (qt.offsets) dev_free(qt.offsets, s);
+    return e;
+}
+
 }  // namespace
+
+cudaError_t count_by_intersection(const Table& t, const void* d_q, uint64_t q, uint32_t* counts, uint64_t* total,
+                                  cudaStream_t s) {
+    if (total) {
+        cudaError_t e = cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (q == 0) return cudaSuccess;
+    if (t.key_bytes == 4) return intersect_impl<uint32_t>(t, static_cast<const uint32_t*>(d_q), q, counts, total, s);
+    return intersect_impl<uint64_t>(t, static_cast<const uint64_t*>(d_q), q, counts, total, s);
+}
 
 cudaError_t probe_count(const Table& t, const void* d_q, uint64_t q, uint32_t* counts, uint64_t* total,
                         cudaStream_t s) {

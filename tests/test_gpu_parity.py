@@ -50,6 +50,12 @@ def _run_one(hg, ref, keys, B, seed, queries, values, flags, check_gather):
         got = from_dev(counts, np.uint32).astype(np.uint64)
         assert np.array_equal(got, want), "counts differ"
         assert int(from_dev(total, np.uint64)[0]) == int(want.sum())
+        # the paper's query form: HG(Q), then bucket-by-bucket intersection
+        c3 = torch.full((queries.size,), -1, dtype=torch.int32, device="cuda")
+        t3 = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        hg.hg_query_count_intersect(t, dq, c3, t3)
+        assert np.array_equal(from_dev(c3, np.uint32).astype(np.uint64), want), "intersection counts differ"
+        assert int(from_dev(t3, np.uint64)[0]) == int(want.sum())
         # counts only, then total only (join)
         counts2 = torch.full((queries.size,), -1, dtype=torch.int32, device="cuda")
         hg.hg_query_count(t, dq, counts2, None)
