@@ -42,9 +42,11 @@ def parse():
     p.add_argument("--cpu-sample-log2", type=int, default=27)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="zipf_large", choices=["zipf_large", "batched", "serving"],
+    p.add_argument("--workload", default="zipf_large", choices=["zipf_large", "batched", "serving", "dupsweep"],
                    help="zipf_large: the 2^28 build+probe step; batched: 4096 tables in one persistent launch; "
-                        "serving: a Poisson stream of build and probe requests through the serving engine")
+                        "serving: a Poisson stream of build and probe requests through the serving engine; "
+                        "dupsweep: the duplicate-key experiment (each value 2^d times, B = N / 2^d)")
+    p.add_argument("--sweep-log2n", type=int, default=26, help="dupsweep: log2 of keys (and queries)")
     p.add_argument("--requests", type=int, default=200_000, help="serving: requests in the stream")
     p.add_argument("--query-form", default="probe", choices=["probe", "intersect"],
                    help="zipf_large: hg_query_count (grouped probe) or hg_query_count_intersect (HG(Q) + "
@@ -682,6 +684,61 @@ def run_serving(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+DUP_METRIC = "duplicate-key sweep: build and query Gkeys/s vs copies per value"
+
+
+def run_dupsweep(args, rank, world, local_rank):
+    """The paper's duplicate-key experiment: N fixed, every value occurring
+    2^d times (B = N / 2^d); build and query rates timed separately."""
+    import numpy as np
+    import torch
+
+    import paper_2104_00792_gb300 as hg
+    import workloads as W
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if rank != 0:
+        return
+    n = 1 << args.sweep_log2n
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    rows = []
+    for d in range(0, 11):
+        wl = W.duplicate_keys(n, dup_log2=d, salt=d)
+        keys = torch.from_numpy(wl.keys.view(np.int32)).to(dev)
+        queries = torch.from_numpy(wl.queries.view(np.int32)).to(dev)
+        counts = torch.empty(n, dtype=torch.int32, device=dev)
+        total = torch.empty(1, dtype=torch.int64, device=dev)
+        B = wl.num_buckets
+        tb, tq = [], []
+        for rep in range(4):
+            ev[0].record(stream)
+            t = hg.hg_build(keys, B, 0, stream=stream)
+            ev[1].record(stream)
+            hg.hg_query_count(t, queries, counts, total, stream=stream)
+            ev[2].record(stream)
+            torch.cuda.synchronize(dev)
+            if rep:
+                tb.append(ev[0].elapsed_time(ev[1]))
+                tq.append(ev[1].elapsed_time(ev[2]))
+            if rep == 3:
+                walk = hg.hg_probe_stats(t, queries, stream=stream)
+            t.free(stream)
+        mb, mq = statistics.median(tb), statistics.median(tq)
+        rows.append({"copies_log2": d, "buckets": B, "build_ms": mb, "query_ms": mq,
+                     "build_gkeys_per_s": n / (mb * 1e-3) / 1e9, "query_gkeys_per_s": n / (mq * 1e-3) / 1e9,
+                     "walked_keys_per_query": walk["walked"] / n})
+        del keys, queries, counts
+    line = {"metric": DUP_METRIC, "value": rows[-1]["query_gkeys_per_s"], "unit": "Gkeys/s", "n_gpus": 1,
+            "steps": 3, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"duplicate_keys: N = Q = 2^{args.sweep_log2n} uint32 keys over N / 2^d values "
+                                   f"(B = N / 2^d), queries 50% hits; d = 0..10"},
+            "sweep": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -693,6 +750,8 @@ def main():
         run_batched(args, rank, world, local_rank)
     elif args.workload == "serving":
         run_serving(args, rank, world, local_rank)
+    elif args.workload == "dupsweep":
+        run_dupsweep(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

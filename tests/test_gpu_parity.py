@@ -275,3 +275,10 @@ def test_grouped_probe_one_pass(hg):
 def test_grouped_probe_u64(hg):
     wl = W.join_kv(n=(1 << 22) + (1 << 20), num_buckets=(1 << 22) - 9, q=(1 << 21) + 1, salt=10)
     _probe_only(hg, wl.keys, (1 << 22) - 9, wl.queries, values=wl.values)
+
+
+@pytest.mark.parametrize("dup_log2", [0, 3, 6, 9, 12])
+def test_duplicate_key_sweep(hg, dup_log2):
+    """The duplicate-key experiment's inputs: every value about 2^d times, B = N / 2^d."""
+    wl = W.duplicate_keys((1 << 16) + 5, dup_log2=dup_log2, q=(1 << 14) + 3, salt=dup_log2)
+    _run_all(hg, wl.keys, wl.num_buckets, 0, wl.queries, check_gather=False)

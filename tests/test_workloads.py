@@ -103,3 +103,15 @@ def test_batched_uniform_recipe():
     k0, _, _ = b.table(0)
     k1, _, _ = b.table(1)
     assert not np.array_equal(k0[:16], k1[:16])
+
+
+def test_duplicate_keys_recipe():
+    wl = W.duplicate_keys(1 << 16, dup_log2=5, salt=2)
+    V = (1 << 16) >> 5
+    assert wl.num_buckets == V and wl.keys.max() < V
+    # every value occurs about 2^5 times
+    occ = np.bincount(wl.keys, minlength=V)
+    assert abs(occ.mean() - 32) < 1e-9 and occ.min() > 5
+    hits = wl.queries < V
+    assert 0.45 < hits.mean() < 0.55
+    assert np.all(wl.queries[~hits] >= V)  # misses are absent values

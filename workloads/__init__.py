@@ -21,6 +21,10 @@ Recipes (master seed ``MASTER_SEED``; stream ids in ``STREAM``):
   whose ``hot_frac`` share of slots holds ``rep`` copies each of hot keys;
   every distinct probe key is a build key with probability 1/2, else fresh;
   slots are Fisher-Yates shuffled.
+* ``duplicate_keys`` -- the duplicate-key experiment (Sec. 5.5): N keys
+  uniform over a value range of V = N / 2^d values, so every value occurs
+  about 2^d times, with B = V buckets; queries hit (a uniform value of the
+  range) with probability ``hit``, else miss (a value above the range).
 * ``batched_uniform`` -- many independent tables: table t has
   N_t = round(2^(lo + (hi - lo) u_t)) keys (u_t uniform in [0, 1) from the
   ``sizes`` stream, so sizes are log-uniform), B_t = N_t buckets, and N_t
@@ -379,3 +383,19 @@ def serving_trace(n_requests: int = 200_000, build_frac: float = 0.3, build_log2
 def serve_table_n(trace: list) -> dict:
     """table id -> number of keys, from the trace's builds."""
     return {r.table: r.size for r in trace if r.kind == "build"}
+
+
+def duplicate_keys(n: int = 1 << 26, dup_log2: int = 0, q: int | None = None, hit: float = 0.5,
+                   master: int = MASTER_SEED, salt: int = 0) -> Workload:
+    """N keys over V = N >> dup_log2 values (each value about 2^dup_log2 times), B = V."""
+    q = n if q is None else q
+    V = max(1, n >> dup_log2)
+    raw = uniform_u32(stream("keys", master, salt), n).astype(np.uint64)
+    keys = ((raw * np.uint64(V)) >> np.uint64(32)).astype(np.uint32)
+    sel = uniform_u64(stream("q_select", master, salt), q)
+    hits = (sel >> np.uint64(32)) < np.uint64(hit_threshold(hit))
+    low = sel & np.uint64(0xFFFFFFFF)
+    inside = (low * np.uint64(V)) >> np.uint64(32)
+    outside = np.uint64(V) + ((low * np.uint64((1 << 32) - V)) >> np.uint64(32))
+    queries = np.where(hits, inside, outside).astype(np.uint32)
+    return Workload("duplicate_keys", keys, None, queries, V)
