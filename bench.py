@@ -181,6 +181,24 @@ def ncu_traffic(kernel):
     return float(v) if v else None
 
 
+def batch_traffic_ratio():
+    """ncu DRAM bytes per algorithmic byte of the batched kernel, if measured on
+    the current kernel sources (else None)."""
+    try:
+        rows = {}
+        with open(os.path.join(ROOT, "profiles", "dram_traffic_batch.txt")) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    rows[k.strip()] = v.strip()
+    except OSError:
+        return None
+    if rows.get("source_hash") != source_hash():
+        return None
+    v = rows.get("traffic_per_model_byte.batch")
+    return float(v) if v else None
+
+
 def cpu_oracle_sample(wl, log2s):
     """Oracle build + count on the first 2^log2s keys and queries of the
     workload, table size scaled to keep the same keys-per-bucket ratio."""
@@ -518,7 +536,10 @@ def run_batched(args, rank, world, local_rank):
                    "keys": N, "queries": Q, "buckets": B, "params": chosen,
                    "l2": f"inputs exceed L2 ({(N + Q) * 4 / 2**30:.1f} GiB read per step); no flush"},
         "roofline": {"bound": "hbm", "kernel": "batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind, "model_bytes": model},
+                     "frac": achieved / peak,
+                     "traffic": (batch_traffic_ratio() * model) if batch_traffic_ratio() else None,
+                     "traffic_note": "ncu DRAM bytes per algorithmic byte at 512 tables x this batch's model bytes",
+                     "peak_kind": peak_kind, "model_bytes": model},
         "vs_plain": {"plain_ms_per_step": plain_ms, "speedup": (plain_ms / ms) if plain_ms else None,
                      "plain": "hg_build + hg_query_count + hg_free per table, same stream",
                      "counts_identical": ok},
