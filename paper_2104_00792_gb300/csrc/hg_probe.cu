@@ -541,26 +541,29 @@ k_walk_stats(const K* __restrict__ qs, uint64_t q, const uint32_t* __restrict__ 
 
 // One table bin per CTA work item (the paper's per-bucket intersection,
 // Sec. 3.3, done a bin of 8192 buckets at a time).  The bin's offsets and
-// (when they fit) keys are brought into shared memory by bulk copies (TMA)
-// while the previous bin's queries are answered from the other buffer, so the
-// copies overlap the work.  Buckets longer than WALK_WARP keys go to the
+// (when they fit) keys are brought into shared memory by bulk copies (TMA);
+// each CTA holds one bin at a time and two CTAs share an SM, so one CTA's
+// copies overlap the other's queries (this measured faster than one CTA of
+// 1024 threads double-buffering two bins).  Buckets longer than WALK_WARP keys go to the
 // long-bucket list as in the direct probe; a bin whose keys do not fit is
 // walked in global memory.  Equal query keys share a bucket, hence a bin: for
 // 32-bit keys, the count of every warp-walked bucket is kept in a small
 // per-bin shared-memory table, so a key queried again in the same bin is
 // answered without walking (the per-bucket list intersection of Sec. 3.3
 // matches each distinct query key once).  Every wait on a copy is bounded.
-constexpr uint32_t BIN_KEY_BYTES = 78 * 1024;                                  // per buffer
+constexpr uint32_t BIN_KEY_BYTES = 72 * 1024;                                  // per buffer
 constexpr uint32_t BIN_OFF_BYTES = ((BIN_BUCKETS + 1) * 4 + 15) / 16 * 16;     // 8193 offsets, rounded to 16 B
 constexpr uint32_t BIN_BUF_BYTES = BIN_OFF_BYTES + BIN_KEY_BYTES;
-constexpr int BIN_PROBE_THREADS = 1024;
+constexpr int BIN_PROBE_THREADS = 512;
+constexpr int BIN_PROBE_CTAS_PER_SM = 2;
+constexpr int BIN_BUFFERS = 1;  // bins in flight per CTA (2 = double buffering within the CTA)
 constexpr uint32_t COPY_WAIT_LIMIT = 1u << 26;  // polls of a copy's barrier (far beyond any real copy)
 constexpr uint32_t CACHE_SLOTS = 512;           // per-bin (key, count) table; linear probing
 constexpr uint32_t CACHE_PROBES = 8;
 constexpr unsigned long long CACHE_EMPTY = ~0ull;  // a count never reaches 2^32 - 1 here
 
 template <typename K, int OUT, bool TOTAL>
-__global__ void __launch_bounds__(BIN_PROBE_THREADS, 1)
+__global__ void __launch_bounds__(BIN_PROBE_THREADS, BIN_PROBE_CTAS_PER_SM)
 k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, uint32_t nbins,
              const K* __restrict__ keys, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
              uint64_t* total, LongSink L, uint32_t* work_ctr, uint32_t* err) {
@@ -568,6 +571,7 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_bin[2], s_k0[2], s_klo[2], s_staged[2];
+    static_assert(BIN_BUFFERS == 1 || BIN_BUFFERS == 2, "one or two bin buffers");
     constexpr bool CACHE = sizeof(K) == 4;
     __shared__ unsigned long long s_cache[CACHE ? CACHE_SLOTS : 1];  // (count << 32 | key)
     const unsigned lane = lane_id();
@@ -603,12 +607,14 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
         bulk_load(buf, offs + b0, off_bytes, &s_bar[b]);
         if (staged && key_bytes) bulk_load(buf + BIN_OFF_BYTES, keys + klo, key_bytes, &s_bar[b]);
     };
-    if (threadIdx.x == 0) issue(0);
+    if (BIN_BUFFERS == 2 && threadIdx.x == 0) issue(0);
     uint32_t phase0 = 0, phase1 = 0;
     int cur = 0;
     bool failed = false;
     while (true) {
-        if (threadIdx.x == 0) issue(cur ^ 1);  // the previous user of that buffer finished at the last barrier
+        // the buffer's previous user finished at the last barrier: with two buffers
+        // the next bin's copies start now, with one the current bin's
+        if (threadIdx.x == 0) issue(BIN_BUFFERS == 2 ? (cur ^ 1) : 0);
         if (CACHE)
             for (uint32_t t = threadIdx.x; t < CACHE_SLOTS; t += blockDim.x) s_cache[t] = CACHE_EMPTY;
         __syncthreads();
@@ -710,7 +716,7 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
             }
         }
         __syncthreads();
-        cur ^= 1;
+        if (BIN_BUFFERS == 2) cur ^= 1;
     }
     if (failed) {
         // a copy never completed (not expected): record it, give the other buffer's
@@ -718,7 +724,7 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
         if (threadIdx.x == 0) {
             atomicOr(err, DEVERR_TIMEOUT);
             const int other = cur ^ 1;
-            if (s_bin[other] < nbins) {
+            if (BIN_BUFFERS == 2 && s_bin[other] < nbins) {
                 const uint32_t ph = other ? phase1 : phase0;
                 uint32_t polls = 0;
                 while (!mbar_test_parity(&s_bar[other], ph) && ++polls < COPY_WAIT_LIMIT) {
@@ -740,7 +746,7 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
     const K* qs = static_cast<const K*>(g.q_grouped);
     {
         auto kern = k_probe_bins<K, OUT, TOTAL>;
-        const size_t smem = 2 * (size_t)BIN_BUF_BYTES;
+        const size_t smem = BIN_BUFFERS * (size_t)BIN_BUF_BYTES;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
