@@ -240,6 +240,71 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def e2e_pipelined(hg, wl, query, dev, stream, steps, barrier):
+    """End to end through the C ABI with host buffers: every step copies its
+    keys and queries in from pinned host memory, builds, counts, and copies
+    the counts and total back.  Copies run on their own streams and two
+    device buffer sets alternate, so one step's copies overlap another's
+    kernels (the pipelining a caller of the library would use)."""
+    import numpy as np
+    import torch
+
+    N, Q, B = wl.keys.size, wl.queries.size, wl.num_buckets
+    h_keys = torch.from_numpy(wl.keys.view(np.int32)).pin_memory()
+    h_q = torch.from_numpy(wl.queries.view(np.int32)).pin_memory()
+    sets = []
+    for _ in range(2):
+        sets.append({"keys": torch.empty(N, dtype=torch.int32, device=dev),
+                     "queries": torch.empty(Q, dtype=torch.int32, device=dev),
+                     "counts": torch.empty(Q, dtype=torch.int32, device=dev),
+                     "total": torch.empty(1, dtype=torch.int64, device=dev),
+                     "h_counts": torch.empty(Q, dtype=torch.int32).pin_memory(),
+                     "h_total": torch.empty(1, dtype=torch.int64).pin_memory(),
+                     "in_done": torch.cuda.Event(), "out_done": torch.cuda.Event(),
+                     "used": torch.cuda.Event()})
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def e2e_step(k):
+        st = sets[k % 2]
+        if k >= 2:
+            s_in.wait_event(st["used"])          # the set's previous inputs are consumed
+        with torch.cuda.stream(s_in):
+            st["keys"].copy_(h_keys, non_blocking=True)
+            st["queries"].copy_(h_q, non_blocking=True)
+            st["in_done"].record(s_in)
+        stream.wait_event(st["in_done"])
+        if k >= 2:
+            stream.wait_event(st["out_done"])    # its previous counts have left the device
+        t = hg.hg_build(st["keys"], B, 0, stream=stream)
+        query(t, st["queries"], st["counts"], st["total"], stream=stream)
+        t.free(stream)
+        st["used"].record(stream)
+        s_out.wait_event(st["used"])
+        with torch.cuda.stream(s_out):
+            st["h_counts"].copy_(st["counts"], non_blocking=True)
+            st["h_total"].copy_(st["total"], non_blocking=True)
+            st["out_done"].record(s_out)
+
+    for k in range(2):
+        e2e_step(k)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e_steps = max(4, steps // 3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s_in.wait_event(ev0)
+    for k in range(e_steps):
+        e2e_step(k)
+    for st in sets:
+        stream.wait_event(st["out_done"])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    last = sets[(e_steps - 1) % 2]
+    ok = int(last["h_total"].numpy().view(np.uint64)[0]) == int(last["h_counts"].numpy().view(np.uint32).sum(dtype=np.uint64))
+    return {"ms": ev0.elapsed_time(ev1) / e_steps, "h2d": 4 * (N + Q), "d2h": 4 * Q + 8, "check": ok}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -304,31 +369,7 @@ def run_ours(args, rank, world, local_rank):
         # counts and total copied out, inside the timed region
         e2e = None
         if not args.no_e2e:
-            h_keys = torch.from_numpy(wl.keys.view(np.int32)).pin_memory()
-            h_q = torch.from_numpy(wl.queries.view(np.int32)).pin_memory()
-            h_counts = torch.empty(Q, dtype=torch.int32).pin_memory()
-            h_total = torch.empty(1, dtype=torch.int64).pin_memory()
-
-            def e2e_step():
-                keys.copy_(h_keys, non_blocking=True)
-                queries.copy_(h_q, non_blocking=True)
-                step()
-                h_counts.copy_(counts, non_blocking=True)
-                h_total.copy_(total, non_blocking=True)
-
-            for _ in range(2):
-                e2e_step()
-            torch.cuda.synchronize(dev)
-            barrier()
-            e_steps = max(3, args.steps // 3)
-            ev0.record(stream)
-            for _ in range(e_steps):
-                e2e_step()
-            ev1.record(stream)
-            torch.cuda.synchronize(dev)
-            barrier()
-            e2e_ms = ev0.elapsed_time(ev1) / e_steps
-            e2e = {"ms": e2e_ms, "h2d": 4 * (N + Q), "d2h": 4 * Q + 8}
+            e2e = e2e_pipelined(hg, wl, query, dev, stream, args.steps, barrier)
         time.sleep(0.2)
 
     # max over ranks
@@ -408,7 +449,8 @@ def run_ours(args, rank, world, local_rank):
     if e2e:
         line["e2e"] = {"value": aggregate_gkeys(world, N + Q, e2e["ms"]), "unit": UNIT,
                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
-                       "ms_per_step": e2e["ms"]}
+                       "ms_per_step": e2e["ms"], "total_equals_sum_of_counts": e2e["check"],
+                       "pipelining": "copies on their own streams, two device buffer sets alternating"}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(wl, args.cpu_sample_log2)
     print(json.dumps(line), flush=True)
@@ -469,28 +511,55 @@ def run_batched(args, rank, world, local_rank):
         launches = hg.hg_launch_count() - launches0
         ms = ev0.elapsed_time(ev1) / args.steps
         # end to end through the C ABI with host buffers: pinned keys and queries
-        # copied in, counts copied out, every step
+        # copied in, counts copied out, every step; copies on their own streams,
+        # two buffer sets (and two batch plans) alternating
         e2e_ms = None
         if not args.no_e2e:
             h_keys = torch.from_numpy(wl.keys.view(np.int32)).pin_memory()
             h_q = torch.from_numpy(wl.queries.view(np.int32)).pin_memory()
-            h_counts = torch.empty(Q, dtype=torch.int32).pin_memory()
+            b2 = hg.hg_batch_create(wl.key_offsets, wl.num_buckets, wl.query_offsets, stream=stream)
+            hg.hg_batch_set_params(b2, chosen["threads"], chosen["bin_shift"], chosen["fuse_keys"])
+            sets = []
+            for plan, kk, qq, cc in ((b, keys, queries, counts),
+                                     (b2, torch.empty_like(keys), torch.empty_like(queries), torch.empty_like(counts))):
+                sets.append({"plan": plan, "keys": kk, "queries": qq, "counts": cc,
+                             "h_counts": torch.empty(Q, dtype=torch.int32).pin_memory(),
+                             "in_done": torch.cuda.Event(), "out_done": torch.cuda.Event(),
+                             "used": torch.cuda.Event()})
+            s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
-            def e2e_step():
-                keys.copy_(h_keys, non_blocking=True)
-                queries.copy_(h_q, non_blocking=True)
-                hg.hg_batch_run(b, keys, queries, counts, stream=stream)
-                h_counts.copy_(counts, non_blocking=True)
+            def e2e_step(k):
+                st = sets[k % 2]
+                if k >= 2:
+                    s_in.wait_event(st["used"])
+                with torch.cuda.stream(s_in):
+                    st["keys"].copy_(h_keys, non_blocking=True)
+                    st["queries"].copy_(h_q, non_blocking=True)
+                    st["in_done"].record(s_in)
+                stream.wait_event(st["in_done"])
+                if k >= 2:
+                    stream.wait_event(st["out_done"])
+                hg.hg_batch_run(st["plan"], st["keys"], st["queries"], st["counts"], stream=stream)
+                st["used"].record(stream)
+                s_out.wait_event(st["used"])
+                with torch.cuda.stream(s_out):
+                    st["h_counts"].copy_(st["counts"], non_blocking=True)
+                    st["out_done"].record(s_out)
 
-            e2e_step()
+            for k in range(2):
+                e2e_step(k)
             torch.cuda.synchronize(dev)
-            e_steps = max(3, args.steps // 3)
+            e_steps = max(4, args.steps // 3)
             ev0.record(stream)
-            for _ in range(e_steps):
-                e2e_step()
+            s_in.wait_event(ev0)
+            for k in range(e_steps):
+                e2e_step(k)
+            for st in sets:
+                stream.wait_event(st["out_done"])
             ev1.record(stream)
             torch.cuda.synchronize(dev)
             e2e_ms = ev0.elapsed_time(ev1) / e_steps
+            b2.free(stream)
         time.sleep(0.2)
     ms, e2e_v = max_over_ranks([ms, e2e_ms or 0.0], dist, dev)
     if e2e_ms is not None:
