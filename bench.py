@@ -48,9 +48,10 @@ def parse():
                         "dupsweep: the duplicate-key experiment (each value 2^d times, B = N / 2^d)")
     p.add_argument("--sweep-log2n", type=int, default=26, help="dupsweep: log2 of keys (and queries)")
     p.add_argument("--requests", type=int, default=200_000, help="serving: requests in the stream")
-    p.add_argument("--query-form", default="probe", choices=["probe", "intersect"],
-                   help="zipf_large: hg_query_count (grouped probe) or hg_query_count_intersect (HG(Q) + "
-                        "bucket intersections, the paper's query form)")
+    p.add_argument("--query-form", default="plan", choices=["plan", "probe", "intersect"],
+                   help="zipf_large: plan = hg_query_plan_create on a second stream while the table builds, then "
+                        "hg_query_count_plan; probe = hg_query_count after the build; intersect = "
+                        "hg_query_count_intersect (HG(Q) + bucket intersections, the paper's query form)")
     p.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / the plain path's capacity")
     p.add_argument("--budget-gb", type=float, default=100.0, help="serving: device-memory budget for tables")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
@@ -240,7 +241,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def e2e_pipelined(hg, wl, query, dev, stream, steps, barrier):
+def e2e_pipelined(hg, wl, build_and_query, dev, stream, steps, barrier):
     """End to end through the C ABI with host buffers: every step copies its
     keys and queries in from pinned host memory, builds, counts, and copies
     the counts and total back.  Copies run on their own streams and two
@@ -275,9 +276,7 @@ def e2e_pipelined(hg, wl, query, dev, stream, steps, barrier):
         stream.wait_event(st["in_done"])
         if k >= 2:
             stream.wait_event(st["out_done"])    # its previous counts have left the device
-        t = hg.hg_build(st["keys"], B, 0, stream=stream)
-        query(t, st["queries"], st["counts"], st["total"], stream=stream)
-        t.free(stream)
+        build_and_query(st["keys"], st["queries"], st["counts"], st["total"], stream)
         st["used"].record(stream)
         s_out.wait_event(st["used"])
         with torch.cuda.stream(s_out):
@@ -330,12 +329,31 @@ def run_ours(args, rank, world, local_rank):
     total = torch.empty(1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    query = hg.hg_query_count_intersect if args.query_form == "intersect" else hg.hg_query_count
+    side = torch.cuda.Stream(dev)
+    joined = torch.cuda.Event()
+
+    forked = torch.cuda.Event()
+    query = {"probe": hg.hg_query_count, "intersect": hg.hg_query_count_intersect}.get(args.query_form)
+
+    def build_and_query(k, qs, c, tot, stream):
+        if args.query_form == "plan":
+            # the queries are grouped on a second stream while the table builds: the
+            # plan needs only the table's shape, which hg_build fixes on return
+            forked.record(stream)                 # inputs are ready here
+            t = hg.hg_build(k, B, 0, stream=stream)
+            side.wait_event(forked)
+            plan = hg.hg_query_plan_create(t, qs, stream=side)
+            joined.record(side)
+            stream.wait_event(joined)
+            hg.hg_query_count_plan(t, plan, c, tot, stream=stream)
+            plan.free(stream)
+        else:
+            t = hg.hg_build(k, B, 0, stream=stream)
+            query(t, qs, c, tot, stream=stream)
+        t.free(stream)
 
     def step():
-        t = hg.hg_build(keys, B, 0, stream=stream)
-        query(t, queries, counts, total, stream=stream)
-        t.free(stream)
+        build_and_query(keys, queries, counts, total, stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -369,7 +387,7 @@ def run_ours(args, rank, world, local_rank):
         # counts and total copied out, inside the timed region
         e2e = None
         if not args.no_e2e:
-            e2e = e2e_pipelined(hg, wl, query, dev, stream, args.steps, barrier)
+            e2e = e2e_pipelined(hg, wl, build_and_query, dev, stream, args.steps, barrier)
         time.sleep(0.2)
 
     # max over ranks
@@ -433,9 +451,11 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": workload_desc(args.log2n), "parallelism": f"replicas{world}",
                    "l2": "inputs exceed L2 (2 GiB read per step); no flush",
-                   "step": ("hg_build + hg_query_count_intersect(counts, total) + hg_free"
-                            if args.query_form == "intersect" else
-                            "hg_build + hg_query_count(counts, total) + hg_free")},
+                   "step": {"plan": "hg_build, with hg_query_plan_create on a second stream, then "
+                                    "hg_query_count_plan(counts, total) + hg_free",
+                            "probe": "hg_build + hg_query_count(counts, total) + hg_free",
+                            "intersect": "hg_build + hg_query_count_intersect(counts, total) + hg_free"}
+                   [args.query_form]},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(dom), "peak_kind": peak_kind,
                      "step_model_bytes": step_bytes,

@@ -119,6 +119,24 @@ hg_status hg_query_gather(const hg_table* t, const void* d_queries, uint64_t q, 
                           uint32_t* d_out_values, uint64_t out_capacity, uint64_t* h_total, hg_stream_t s);
 
 /*
+ * Query plans: hg_query_count split in two, so that preparing the queries can
+ * overlap the table's build.  hg_query_plan_create reads d_queries and only
+ * the table's bucket count, seed and size (not its arrays, which may still be
+ * being built on another stream) and groups the queries by the table's bins
+ * when that pays (large query sets against tables larger than L2), else keeps
+ * the pointer.  hg_query_count_plan then writes the same counts and total as
+ * hg_query_count; order it after both the build and the plan creation (for
+ * example with cudaStreamWaitEvent).  d_queries must stay valid until the
+ * count has completed.  hg_query_plan_free is stream-ordered on `s`.
+ */
+typedef struct hg_query_plan hg_query_plan; /* opaque; owns the grouped queries and scratch */
+hg_status hg_query_plan_create(const hg_table* t, const void* d_queries, uint64_t q, hg_stream_t s,
+                               hg_query_plan** out);
+hg_status hg_query_count_plan(const hg_table* t, const hg_query_plan* p, uint32_t* d_counts, uint64_t* d_total,
+                              hg_stream_t s);
+hg_status hg_query_plan_free(hg_query_plan* p, hg_stream_t s);
+
+/*
  * hg_query_count_intersect -- the same per-slot counts (and total) as
  * hg_query_count, computed by the paper's query form (Sec. 3.3): build
  * HG(Q), a HashGraph of the queries with the table's num_buckets and seed

@@ -53,6 +53,11 @@ lib.hg_query_count.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp]
 lib.hg_query_gather.argtypes = [_vp, _vp, _u64, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]
 lib.hg_join_count.argtypes = [_vp, _vp, _u64, _vp, _vp]
 lib.hg_query_count_intersect.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp]
+lib.hg_query_plan_create.argtypes = [_vp, _vp, _u64, _vp, ctypes.POINTER(_vp)]
+lib.hg_query_count_plan.argtypes = [_vp, _vp, _vp, _vp, _vp]
+lib.hg_query_plan_free.argtypes = [_vp, _vp]
+for _f in ("hg_query_plan_create", "hg_query_count_plan", "hg_query_plan_free"):
+    getattr(lib, _f).restype = ctypes.c_int
 lib.hg_query_count_intersect.restype = ctypes.c_int
 lib.hg_free.argtypes = [_vp, _vp]
 lib.hg_sync.argtypes = [_vp, _vp]
@@ -160,6 +165,49 @@ def hg_query_count_intersect(table: Table, queries: torch.Tensor, counts: torch.
     """hg_query_count_intersect: the same counts by the paper's query form (HG(Q), then bucket intersections)."""
     _check(lib.hg_query_count_intersect(table.handle, _ptr(queries), queries.numel(), _ptr(counts), _ptr(total),
                                         _stream(stream)))
+    return counts, total
+
+
+class QueryPlan:
+    """Queries prepared for counting against one table (owns the library's hg_query_plan*)."""
+
+    def __init__(self, handle: int, queries: torch.Tensor, stream: int):
+        self.handle = handle
+        self.queries = queries  # kept alive: the count may read it
+        self._stream = stream
+
+    def free(self, stream=None):
+        """Stream-ordered free on `stream` (default: the current stream, where the count usually ran)."""
+        if self.handle:
+            _check(lib.hg_query_plan_free(self.handle, _stream(stream)))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hg_query_plan_create(table: Table, queries: torch.Tensor, stream=None) -> QueryPlan:
+    """Group the queries by the table's bins (needs only the table's shape, so it may
+    run on another stream while the table is being built)."""
+    h = _vp()
+    s = _stream(stream)
+    _check(lib.hg_query_plan_create(table.handle, _ptr(queries), queries.numel(), s, ctypes.byref(h)))
+    return QueryPlan(h.value, queries, s)
+
+
+def hg_query_count_plan(table: Table, plan: QueryPlan, counts: torch.Tensor | None = None,
+                        total: torch.Tensor | None = None, stream=None):
+    """Counts and/or total of a planned query set (same results as hg_query_count)."""
+    _check(lib.hg_query_count_plan(table.handle, plan.handle, _ptr(counts), _ptr(total), _stream(stream)))
     return counts, total
 
 

@@ -278,6 +278,53 @@ hg_status hg_query_count_intersect(const hg_table* ht, const void* d_queries, ui
     return HG_OK;
 }
 
+hg_status hg_query_plan_create(const hg_table* ht, const void* d_queries, uint64_t q, hg_stream_t s,
+                               hg_query_plan** out) {
+    const Table* t = reinterpret_cast<const Table*>(ht);
+    if (!out) return fail(HG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!t) return fail(HG_ERR_INVALID_ARG, "table is NULL");
+    hg_status st = check_queries(t, d_queries, q);
+    if (st != HG_OK) return st;
+    if ((st = check_device(t)) != HG_OK) return st;
+    QueryPlan* p = new (std::nothrow) QueryPlan();
+    if (!p) return fail(HG_ERR_OOM, "host allocation failed");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+    cudaError_t e = plan_queries(*t, d_queries, q, p, cs);
+    if (e != cudaSuccess) {
+        plan_release(p, cs);
+        delete p;
+        return cuda_fail(e, "hg_query_plan_create");
+    }
+    *out = reinterpret_cast<hg_query_plan*>(p);
+    return HG_OK;
+}
+
+hg_status hg_query_count_plan(const hg_table* ht, const hg_query_plan* hp, uint32_t* d_counts, uint64_t* d_total,
+                              hg_stream_t s) {
+    const Table* t = reinterpret_cast<const Table*>(ht);
+    const QueryPlan* p = reinterpret_cast<const QueryPlan*>(hp);
+    if (!t || !p) return fail(HG_ERR_INVALID_ARG, "table or plan is NULL");
+    if (p->B != t->B || p->seed != t->seed || p->n != t->n || p->key_bytes != t->key_bytes)
+        return fail(HG_ERR_INVALID_ARG, "the plan was made for a table of another shape or seed");
+    if (!d_counts && !d_total && p->q > 0) return fail(HG_ERR_INVALID_ARG, "d_counts and d_total are both NULL");
+    if (d_counts && p->q > 0 && !aligned(d_counts, 4)) return fail(HG_ERR_INVALID_ARG, "d_counts is not 4-byte aligned");
+    if (d_total && !aligned(d_total, 8)) return fail(HG_ERR_INVALID_ARG, "d_total is not 8-byte aligned");
+    hg_status st = check_device(t);
+    if (st != HG_OK) return st;
+    cudaError_t e = count_planned(*t, *p, d_counts, d_total, reinterpret_cast<cudaStream_t>(s));
+    if (e != cudaSuccess) return cuda_fail(e, "hg_query_count_plan");
+    return HG_OK;
+}
+
+hg_status hg_query_plan_free(hg_query_plan* hp, hg_stream_t s) {
+    QueryPlan* p = reinterpret_cast<QueryPlan*>(hp);
+    if (!p) return HG_OK;
+    plan_release(p, reinterpret_cast<cudaStream_t>(s));
+    delete p;
+    return HG_OK;
+}
+
 hg_status hg_join_count(const hg_table* ht, const void* d_queries, uint64_t q, uint64_t* d_total, hg_stream_t s) {
     const Table* t = reinterpret_cast<const Table*>(ht);
     if (!t) return fail(HG_ERR_INVALID_ARG, "table is NULL");

@@ -90,6 +90,7 @@ struct GroupedQueries {
     const uint32_t* dr_b = nullptr;
     const uint2* lb_a = nullptr;
     const uint2* lb_b = nullptr;
+    uint32_t* err = nullptr;  // error word of the grouping and reverse kernels (null: the table's)
 };
 bool probe_grouping_pays(const Table& t, uint64_t q);
 cudaError_t group_queries(const Table& t, const void* d_q, uint64_t q, GroupedQueries* g, cudaStream_t s);
@@ -115,6 +116,22 @@ cudaError_t gather_offsets(const Table& t, const void* d_q, uint64_t q, uint64_t
 cudaError_t gather_values(const Table& t, const void* d_q, uint64_t q, const uint64_t* out_offsets,
                           uint32_t* out_values, GatherCtx* ctx, cudaStream_t s);
 void gather_release(GatherCtx* ctx, cudaStream_t s);
+
+// Queries prepared for counting against a table: grouped by the table's bins
+// when grouping pays (needs only the table's bucket count, seed and size, not
+// its arrays, so it may run while the table is being built), else kept as given.
+struct QueryPlan {
+    const void* queries = nullptr;
+    uint64_t q = 0;
+    bool grouped = false;
+    GroupedQueries g;
+    uint32_t* err = nullptr;  // the plan's own device error word
+    uint64_t B = 0, seed = 0, n = 0;  // the table it was made for
+    uint32_t key_bytes = 0;
+};
+cudaError_t plan_queries(const Table& t, const void* d_q, uint64_t q, QueryPlan* p, cudaStream_t s);
+cudaError_t count_planned(const Table& t, const QueryPlan& p, uint32_t* counts, uint64_t* total, cudaStream_t s);
+void plan_release(QueryPlan* p, cudaStream_t s);
 
 // The paper's query form: HG(Q) built with the table's buckets and seed, then
 // bucket-by-bucket intersection with the table; per-slot counts as probe_count.

@@ -1265,7 +1265,7 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
         if (r != cudaSuccess) return r;
         launch_begin("q_partition", s);
         kern<<<grid, PASS_THREADS, smem, s>>>(in, nullptr, nq, t.H, sh, mask, R, cm, nch_host, plan, cbase, out,
-                                              nullptr, t.err, dr, lb);
+                                              nullptr, (g->err ? g->err : t.err), dr, lb);
         launch_end("q_partition", s);
         return cudaGetLastError();
     };
@@ -1306,7 +1306,7 @@ cudaError_t ungroup_counts_impl(const Table& t, const GroupedQueries* g, const u
     if (g->two) {
         launch_begin("q_reverse", s);
         k_pass_reverse<K><<<g->nch_b_max, PASS_THREADS, 0, s>>>(cs, tmp, g->cm_b, 0u, plan, g->dr_b, g->lb_b,
-                                                               t.err);
+                                                               (g->err ? g->err : t.err));
         launch_end("q_reverse", s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1314,7 +1314,7 @@ cudaError_t ungroup_counts_impl(const Table& t, const GroupedQueries* g, const u
     }
     launch_begin("q_reverse", s);
     k_pass_reverse<K><<<g->nch_a, PASS_THREADS, 0, s>>>(cs, counts, g->cm_a, g->nch_a, plan, g->dr_a, g->lb_a,
-                                                       t.err);
+                                                       (g->err ? g->err : t.err));
     launch_end("q_reverse", s);
     return cudaGetLastError();
 }

@@ -772,45 +772,68 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
     return launch_long_copy<OUT>(L, counts, s);
 }
 
+// Counts of queries already grouped by the table's bins (see group_queries).
 template <typename K>
-cudaError_t count_impl(const Table& t, const K* qs, uint64_t q, uint32_t* counts, uint64_t* total, cudaStream_t s) {
+cudaError_t count_grouped(const Table& t, const GroupedQueries& g, uint64_t q, uint32_t* counts, uint64_t* total,
+                          cudaStream_t s) {
     void* mem = nullptr;
     LongList L{};
     const uint32_t cap = (uint32_t)(q < COUNT_LONG_CAP ? q : COUNT_LONG_CAP);
     cudaError_t e = alloc_list(cap, false, s, &mem, &L);
     if (e != cudaSuccess) return e;
-
-    // Large query sets against a table larger than L2: build the query-side
-    // grouping of the paper's query method (Sec. 3.3: queries bucketed like the
-    // table, each group answered against its own slice of the table), probe
-    // group by group while the slice sits in L1, then put counts back in slot order.
-    if (probe_grouping_pays(t, q)) {
-        GroupedQueries g;
-        e = group_queries(t, qs, q, &g, s);
-        void* cmem = nullptr;
-        const size_t cbytes = ((q + 4) * 4 + 255) & ~size_t(255);
-        if (e == cudaSuccess) e = dev_alloc(&cmem, 256 + (counts ? 2 * cbytes : 0), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cmem, 0, 256, s);
-        if (e == cudaSuccess) {
-            uint32_t* work_ctr = static_cast<uint32_t*>(cmem);
-            uint32_t* cs = counts ? reinterpret_cast<uint32_t*>(static_cast<char*>(cmem) + 256) : nullptr;
-            uint32_t* tmp = counts ? cs + cbytes / 4 : nullptr;
-            if (counts && total) e = run_probe_bins<K, OUT_U32, true>(t, g, cs, total, L, work_ctr, s);
-            else if (counts) e = run_probe_bins<K, OUT_U32, false>(t, g, cs, nullptr, L, work_ctr, s);
-            else e = run_probe_bins<K, OUT_NONE, true>(t, g, nullptr, total, L, work_ctr, s);
-            if (e == cudaSuccess && counts) e = ungroup_counts(t, &g, cs, tmp, counts, s);
-        }
-        if (cmem) dev_free(cmem, s);
-        group_release(&g, s);
-        dev_free(mem, s);
-        return e;
+    void* cmem = nullptr;
+    const size_t cbytes = ((q + 4) * 4 + 255) & ~size_t(255);
+    e = dev_alloc(&cmem, 256 + (counts ? 2 * cbytes : 0), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cmem, 0, 256, s);
+    if (e == cudaSuccess) {
+        uint32_t* work_ctr = static_cast<uint32_t*>(cmem);
+        uint32_t* cs = counts ? reinterpret_cast<uint32_t*>(static_cast<char*>(cmem) + 256) : nullptr;
+        uint32_t* tmp = counts ? cs + cbytes / 4 : nullptr;
+        if (counts && total) e = run_probe_bins<K, OUT_U32, true>(t, g, cs, total, L, work_ctr, s);
+        else if (counts) e = run_probe_bins<K, OUT_U32, false>(t, g, cs, nullptr, L, work_ctr, s);
+        else e = run_probe_bins<K, OUT_NONE, true>(t, g, nullptr, total, L, work_ctr, s);
+        if (e == cudaSuccess && counts) e = ungroup_counts(t, &g, cs, tmp, counts, s);
     }
+    if (cmem) dev_free(cmem, s);
+    dev_free(mem, s);
+    return e;
+}
 
+// Counts by walking each query's bucket where it lies in HBM (or L2).
+template <typename K>
+cudaError_t count_direct(const Table& t, const K* qs, uint64_t q, uint32_t* counts, uint64_t* total,
+                         cudaStream_t s) {
+    void* mem = nullptr;
+    LongList L{};
+    const uint32_t cap = (uint32_t)(q < COUNT_LONG_CAP ? q : COUNT_LONG_CAP);
+    cudaError_t e = alloc_list(cap, false, s, &mem, &L);
+    if (e != cudaSuccess) return e;
     if (counts && total) e = run_probe<K, OUT_U32, true, false>(t, qs, q, counts, total, L, nullptr, nullptr, s);
     else if (counts) e = run_probe<K, OUT_U32, false, false>(t, qs, q, counts, nullptr, L, nullptr, nullptr, s);
     else e = run_probe<K, OUT_NONE, true, false>(t, qs, q, nullptr, total, L, nullptr, nullptr, s);
     dev_free(mem, s);
     return e;
+}
+
+template <typename K>
+cudaError_t count_impl(const Table& t, const K* qs, uint64_t q, uint32_t* counts, uint64_t* total, cudaStream_t s) {
+    // Large query sets against a table larger than L2: build the query-side
+    // grouping of the paper's query method (Sec. 3.3: queries bucketed like the
+    // table, each group answered against its own slice of the table), probe
+    // group by group while the slice sits in shared memory, then put counts
+    // back in slot order.
+    if (probe_grouping_pays(t, q)) {
+        GroupedQueries g;
+        cudaError_t e = group_queries(t, qs, q, &g, s);
+        if (e == cudaSuccess) e = count_grouped<K>(t, g, q, counts, total, s);
+        group_release(&g, s);
+        return e;
+    }
+    return count_direct<K>(t, qs, q, counts, total, s);
+}
+
+__global__ void k_merge_err(const uint32_t* __restrict__ from, uint32_t* to) {
+    if (*from) atomicOr(to, *from);
 }
 
 // counts[slot[j]] = src[j]: per-slot counts from counts in HG(Q) order.
@@ -885,6 +908,48 @@ cudaError_t count_by_intersection(const Table& t, const void* d_q, uint64_t q, u
     if (q == 0) return cudaSuccess;
     if (t.key_bytes == 4) return intersect_impl<uint32_t>(t, static_cast<const uint32_t*>(d_q), q, counts, total, s);
     return intersect_impl<uint64_t>(t, static_cast<const uint64_t*>(d_q), q, counts, total, s);
+}
+
+cudaError_t plan_queries(const Table& t, const void* d_q, uint64_t q, QueryPlan* p, cudaStream_t s) {
+    p->queries = d_q;
+    p->q = q;
+    p->B = t.B;
+    p->seed = t.seed;
+    p->n = t.n;
+    p->key_bytes = t.key_bytes;
+    p->grouped = q > 0 && probe_grouping_pays(t, q);
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&p->err), 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, 16, s);
+    if (e != cudaSuccess || !p->grouped) return e;
+    p->g.err = p->err;
+    return group_queries(t, d_q, q, &p->g, s);
+}
+
+cudaError_t count_planned(const Table& t, const QueryPlan& p, uint32_t* counts, uint64_t* total, cudaStream_t s) {
+    if (total) {
+        cudaError_t e = cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (p.q == 0) return cudaSuccess;
+    cudaError_t e;
+    if (!p.grouped) {
+        e = t.key_bytes == 4 ? count_direct<uint32_t>(t, static_cast<const uint32_t*>(p.queries), p.q, counts, total, s)
+                             : count_direct<uint64_t>(t, static_cast<const uint64_t*>(p.queries), p.q, counts, total, s);
+    } else {
+        e = t.key_bytes == 4 ? count_grouped<uint32_t>(t, p.g, p.q, counts, total, s)
+                             : count_grouped<uint64_t>(t, p.g, p.q, counts, total, s);
+    }
+    if (e == cudaSuccess) {  // the plan's kernel-side errors become the table's
+        k_merge_err<<<1, 1, 0, s>>>(p.err, t.err);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+void plan_release(QueryPlan* p, cudaStream_t s) {
+    group_release(&p->g, s);
+    if (p->err) dev_free(p->err, s);
+    p->err = nullptr;
 }
 
 cudaError_t probe_count(const Table& t, const void* d_q, uint64_t q, uint32_t* counts, uint64_t* total,

@@ -50,6 +50,18 @@ def _run_one(hg, ref, keys, B, seed, queries, values, flags, check_gather):
         got = from_dev(counts, np.uint32).astype(np.uint64)
         assert np.array_equal(got, want), "counts differ"
         assert int(from_dev(total, np.uint64)[0]) == int(want.sum())
+        # a query plan made on another stream while the table is being built
+        side = torch.cuda.Stream()
+        ev = torch.cuda.Event()
+        torch.cuda.synchronize()
+        with hg.hg_query_plan_create(t, dq, stream=side) as plan:
+            ev.record(side)
+            torch.cuda.current_stream().wait_event(ev)
+            c4 = torch.full((queries.size,), -1, dtype=torch.int32, device="cuda")
+            t4 = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+            hg.hg_query_count_plan(t, plan, c4, t4)
+            assert np.array_equal(from_dev(c4, np.uint32).astype(np.uint64), want), "planned counts differ"
+            assert int(from_dev(t4, np.uint64)[0]) == int(want.sum())
         # the paper's query form: HG(Q), then bucket-by-bucket intersection
         c3 = torch.full((queries.size,), -1, dtype=torch.int32, device="cuda")
         t3 = torch.full((1,), -1, dtype=torch.int64, device="cuda")
