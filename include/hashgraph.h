@@ -334,6 +334,16 @@ uint64_t hg_server_table_bytes(uint64_t n, uint64_t num_buckets);
 /* Wait for all work and free every table, stream and buffer of the engine; NULL is accepted. */
 hg_status hg_server_free(hg_server* s);
 
+/*
+ * hg_selftest_bounded_wait -- checks the failure path of the kernels' bounded
+ * waits without faulting or hanging the GPU: one prefix-sum tile runs while its
+ * predecessor never does, so its look-back wait for a flag that nothing sets
+ * runs out after about a second and records a timeout.  Synchronises `s`.
+ * Returns HG_ERR_TIMEOUT when the wait ran out and was reported (the expected
+ * outcome); the context stays usable.
+ */
+hg_status hg_selftest_bounded_wait(hg_stream_t s);
+
 /* Number of kernels this process has launched through the library so far. */
 uint64_t hg_launch_count(void);
 

@@ -64,6 +64,8 @@ lib.hg_sync.argtypes = [_vp, _vp]
 lib.hg_table_view.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                               ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
 lib.hg_probe_stats.argtypes = [_vp, _vp, _u64, _vp, _vp]
+lib.hg_selftest_bounded_wait.argtypes = [_vp]
+lib.hg_selftest_bounded_wait.restype = ctypes.c_int
 lib.hg_launch_count.restype = _u64
 lib.hg_prof_enable.argtypes = [ctypes.c_int]
 lib.hg_prof_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)]
@@ -494,3 +496,8 @@ class Server:
             self.free()
         except Exception:
             pass
+
+
+def hg_selftest_bounded_wait(stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status (HG_ERR_TIMEOUT is the expected one)."""
+    return lib.hg_selftest_bounded_wait(_stream(stream))

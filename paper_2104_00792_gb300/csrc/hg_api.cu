@@ -406,6 +406,21 @@ hg_status hg_table_view(const hg_table* ht, const void** d_offsets, const void**
     return HG_OK;
 }
 
+hg_status hg_selftest_bounded_wait(hg_stream_t s) {
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+    uint32_t* err = nullptr;
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&err), sizeof(uint32_t), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t), cs);
+    if (e == cudaSuccess) e = scan_wait_limit_selftest(err, cs);
+    uint32_t h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, cs);
+    if (err) dev_free(err, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "hg_selftest_bounded_wait");
+    if (h & DEVERR_TIMEOUT) return fail(HG_ERR_TIMEOUT, "the look-back wait ran out as intended");
+    return fail(HG_ERR_CUDA, "the look-back wait did not report running out");
+}
+
 hg_status hg_probe_stats(const hg_table* ht, const void* d_queries, uint64_t q, uint64_t* d_stats, hg_stream_t s) {
     const Table* t = reinterpret_cast<const Table*>(ht);
     if (!t) return fail(HG_ERR_INVALID_ARG, "table is NULL");

@@ -145,6 +145,10 @@ cudaError_t probe_stats(const Table& t, const void* d_q, uint64_t q, uint64_t* s
 cudaError_t scan_exclusive_u32(uint32_t* data, uint64_t n, uint32_t* err, cudaStream_t s);
 cudaError_t scan_exclusive_u64(uint64_t* data, uint64_t n, uint32_t* err, cudaStream_t s);
 
+// Runs one scan tile whose predecessor never publishes: its bounded wait runs
+// out (about a second) and records DEVERR_TIMEOUT in *err.
+cudaError_t scan_wait_limit_selftest(uint32_t* err, cudaStream_t s);
+
 // The same scan with caller-provided scratch (16-byte aligned, at least
 // scan_u32_scratch_bytes(data, n) bytes); allocates nothing.
 size_t scan_u32_scratch_bytes(const uint32_t* data, uint64_t n);

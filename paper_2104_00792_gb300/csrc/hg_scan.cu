@@ -199,6 +199,36 @@ cudaError_t launch_scan_into(T* data, uint64_t n, void* scratch, size_t scratch_
 
 }  // namespace
 
+// Self-test of the bounded look-back wait: one CTA of the scan takes tile 1 of
+// a two-tile array while tile 0 never runs, so its wait for tile 0's flag (a
+// flag nothing sets) runs out after SPIN_LIMIT polls, about a second, and the
+// CTA records DEVERR_TIMEOUT in *err and finishes.
+cudaError_t scan_wait_limit_selftest(uint32_t* err, cudaStream_t s) {
+    constexpr uint64_t TILE = (uint64_t)SCAN_WARPS * 4 * 32 * 4;
+    const uint64_t n = 2 * TILE;
+    const size_t flag_bytes = (3 * sizeof(uint32_t) + 15) & ~size_t(15);
+    const size_t bytes = 4 * n + flag_bytes + 2 * 2 * sizeof(uint32_t);
+    void* mem = nullptr;
+    cudaError_t e = dev_alloc(&mem, bytes, s);
+    if (e != cudaSuccess) return e;
+    uint32_t* data = static_cast<uint32_t*>(mem);
+    uint32_t* flags = data + n;
+    uint32_t* ctr = flags + 2;
+    uint32_t* aggs = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(flags) + flag_bytes);
+    uint32_t* pres = aggs + 2;
+    static const uint32_t one = 1;
+    e = cudaMemsetAsync(mem, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctr, &one, sizeof(one), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        launch_begin("scan", s);
+        k_scan_exclusive<uint32_t, 4, 4><<<1, SCAN_THREADS, 0, s>>>(data, n, flags, aggs, pres, ctr, err);
+        launch_end("scan", s);
+        e = cudaGetLastError();
+    }
+    dev_free(mem, s);
+    return e;
+}
+
 size_t scan_u32_scratch_bytes(const uint32_t* data, uint64_t n) {
     const uint64_t tile = (reinterpret_cast<uintptr_t>(data) & 15) == 0 ? (uint64_t)SCAN_WARPS * 4 * 32 * 4
                                                                           : (uint64_t)SCAN_WARPS * 8 * 32 * 1;
