@@ -821,30 +821,35 @@ def run_dupsweep(args, rank, world, local_rank):
         counts = torch.empty(n, dtype=torch.int32, device=dev)
         total = torch.empty(1, dtype=torch.int64, device=dev)
         B = wl.num_buckets
-        tb, tq = [], []
-        for rep in range(4):
-            ev[0].record(stream)
-            t = hg.hg_build(keys, B, 0, stream=stream)
-            ev[1].record(stream)
-            hg.hg_query_count(t, queries, counts, total, stream=stream)
-            ev[2].record(stream)
-            torch.cuda.synchronize(dev)
-            if rep:
-                tb.append(ev[0].elapsed_time(ev[1]))
-                tq.append(ev[1].elapsed_time(ev[2]))
-            if rep == 3:
-                walk = hg.hg_probe_stats(t, queries, stream=stream)
-            t.free(stream)
-        mb, mq = statistics.median(tb), statistics.median(tq)
-        rows.append({"copies_log2": d, "buckets": B, "build_ms": mb, "query_ms": mq,
-                     "build_gkeys_per_s": n / (mb * 1e-3) / 1e9, "query_gkeys_per_s": n / (mq * 1e-3) / 1e9,
-                     "walked_keys_per_query": walk["walked"] / n})
+        row = {"copies_log2": d, "buckets": B}
+        for mode, flags in (("", 0), ("sorted_", hg.HG_SORTED_BUCKETS)):
+            tb, tq = [], []
+            for rep in range(4):
+                ev[0].record(stream)
+                t = hg.hg_build(keys, B, 0, flags=flags, stream=stream)
+                ev[1].record(stream)
+                hg.hg_query_count(t, queries, counts, total, stream=stream)
+                ev[2].record(stream)
+                torch.cuda.synchronize(dev)
+                if rep:
+                    tb.append(ev[0].elapsed_time(ev[1]))
+                    tq.append(ev[1].elapsed_time(ev[2]))
+                if rep == 3 and not flags:
+                    walk = hg.hg_probe_stats(t, queries, stream=stream)
+                t.free(stream)
+            mb, mq = statistics.median(tb), statistics.median(tq)
+            row.update({f"{mode}build_ms": mb, f"{mode}query_ms": mq,
+                        f"{mode}build_gkeys_per_s": n / (mb * 1e-3) / 1e9,
+                        f"{mode}query_gkeys_per_s": n / (mq * 1e-3) / 1e9})
+        row["walked_keys_per_query"] = walk["walked"] / n
+        rows.append(row)
         del keys, queries, counts
     line = {"metric": DUP_METRIC, "value": rows[-1]["query_gkeys_per_s"], "unit": "Gkeys/s", "n_gpus": 1,
             "steps": 3, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"duplicate_keys: N = Q = 2^{args.sweep_log2n} uint32 keys over N / 2^d values "
-                                   f"(B = N / 2^d), queries 50% hits; d = 0..10"},
+                                   f"(B = N / 2^d), queries 50% hits; d = 0..10; each d built plain and with "
+                                   f"HG_SORTED_BUCKETS (the sort counted in the build time)"},
             "sweep": rows}
     print(json.dumps(line), flush=True)
 

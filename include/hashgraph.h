@@ -60,6 +60,11 @@ typedef enum {
 #define HG_PLAIN_BUILD 0x2u   /* force the direct Algorithm 1 build (global atomics, no partition pass) */
 #define HG_PARTITION_BUILD 0x4u /* force the partitioned build (keys binned by bucket range first, the
                                    "efficient HashGraph" of Sec. 3.2) */
+#define HG_SORTED_BUCKETS 0x8u /* after the build, sort the keys (with their values) inside every bucket of at
+                                  most 16384 keys (8192 for 64-bit keys), so that counting a key in such a
+                                  bucket takes two binary searches instead of a walk whose length grows with
+                                  the copies of each key (the duplicate-key regime, Sec. 5.5); offsets and
+                                  bucket contents are unchanged, only their order inside a bucket is fixed */
 
 typedef struct {
     uint32_t key_bytes;   /* 4 or 8 */

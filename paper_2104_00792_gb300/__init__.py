@@ -38,6 +38,7 @@ STATUS_NAMES = {0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_OOM", 3: "HG_ERR
 HG_INDEX_VALUES = 0x1
 HG_PLAIN_BUILD = 0x2
 HG_PARTITION_BUILD = 0x4
+HG_SORTED_BUCKETS = 0x8
 
 
 class hg_config(ctypes.Structure):

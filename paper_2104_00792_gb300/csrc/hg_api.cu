@@ -42,7 +42,7 @@ std::atomic<uint64_t> g_launches{0};
 // ---- per-kernel event timing (diagnostics) ----
 const char* const kKernelNames[] = {"hist", "scan", "scatter", "probe", "long_prep", "long", "gather",
                                     "long_gather", "walk_stats", "part_hist", "part_plan", "chunk_scan", "chunk_count", "part_scatter", "huge_count",
-                                    "huge_scan", "bin_build", "q_part_count", "q_partition", "q_reverse", "batch", "probe_multi", "scatter_counts"};
+                                    "huge_scan", "bin_build", "q_part_count", "q_partition", "q_reverse", "batch", "probe_multi", "scatter_counts", "sort_buckets"};
 struct ProfRecord {
     const char* name;
     cudaEvent_t start, stop;
@@ -201,7 +201,7 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const void* d_value
         return fail(HG_ERR_INVALID_ARG, "num_buckets = %llu, must be in [1, 2^31]",
                     (unsigned long long)cfg->num_buckets);
     if (n >= (1ull << 32)) return fail(HG_ERR_INVALID_ARG, "n = %llu must be < 2^32", (unsigned long long)n);
-    const uint32_t known = HG_INDEX_VALUES | HG_PLAIN_BUILD | HG_PARTITION_BUILD;
+    const uint32_t known = HG_INDEX_VALUES | HG_PLAIN_BUILD | HG_PARTITION_BUILD | HG_SORTED_BUCKETS;
     if (cfg->flags & ~known) return fail(HG_ERR_INVALID_ARG, "unknown flags 0x%x", cfg->flags & ~known);
     if ((cfg->flags & HG_PLAIN_BUILD) && (cfg->flags & HG_PARTITION_BUILD))
         return fail(HG_ERR_INVALID_ARG, "HG_PLAIN_BUILD and HG_PARTITION_BUILD are exclusive");
@@ -238,6 +238,7 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const void* d_value
         return r;
     }
     e = build_table(*t, d_keys, d_values, st);
+    if (e == cudaSuccess && (cfg->flags & HG_SORTED_BUCKETS)) e = sort_buckets(*t, st);
     if (e != cudaSuccess) {
         hg_status r = cuda_fail(e, "hg_build");
         free_table(t, st);

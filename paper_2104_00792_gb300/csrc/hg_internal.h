@@ -65,6 +65,11 @@ cudaError_t build_table(Table& t, const void* d_keys, const void* d_values, cuda
 bool partition_supported(uint64_t B);
 cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values, cudaStream_t s);
 
+// HG_SORTED_BUCKETS: ascending keys inside every bucket of at most
+// sorted_bucket_max(key_bytes) keys (values moved along); run after the build.
+uint32_t sorted_bucket_max(uint32_t key_bytes);
+cudaError_t sort_buckets(Table& t, cudaStream_t s);
+
 // Queries grouped by the table's bins (ranges of 8192 buckets), so that a
 // bin's offsets and keys stay in L1 while its queries are probed; the counts,
 // produced in grouped order, go back to slot order through reverse passes.

@@ -1331,7 +1331,9 @@ cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values
 
 bool probe_grouping_pays(const Table& t, uint64_t q) {
     const uint64_t P = (t.B + BPB - 1) / BPB;
-    if (P < 2 || P > MAX_BINS || q < (1u << 20)) return false;
+    // one CTA answers one bin at a time: with fewer than ~4 bins per SM the bins
+    // (and the walks inside them) are too few and too large to keep the GPU busy
+    if (P < 4ull * (uint64_t)num_sms() || P > MAX_BINS || q < (1u << 20)) return false;
     const uint64_t table_bytes = 4 * (t.B + 1) + (uint64_t)t.key_bytes * t.n;
     return table_bytes > (48ull << 20);  // the table does not stay in L2
 }

@@ -50,6 +50,11 @@ struct LongSink {
 };
 inline LongSink sink_of(const LongList& L) { return LongSink{L.n, L.slot, L.cap}; }
 
+// Longest bucket a probe may count by binary search (0: the table's buckets are not sorted).
+inline uint32_t sorted_limit(const Table& t) {
+    return (t.flags & HG_SORTED_BUCKETS) ? sorted_bucket_max(t.key_bytes) : 0u;
+}
+
 template <typename K>
 __device__ __forceinline__ uint32_t lane_count(const K* __restrict__ keys, uint32_t lo, uint32_t hi, K key) {
     uint32_t c = 0;
@@ -115,6 +120,23 @@ __device__ __forceinline__ T block_sum(T v) {
     return r;  // valid in thread 0
 }
 
+// Count of `key` in the ascending run keys[lo, hi) (a sorted bucket): the first
+// position >= key and the first position > key, by binary search.
+template <typename K>
+__device__ __forceinline__ uint32_t sorted_count(const K* keys, uint32_t lo, uint32_t hi, K key) {
+    uint32_t a = lo, b = hi;
+    while (a < b) {
+        const uint32_t m = (a + b) >> 1;
+        if (keys[m] < key) a = m + 1; else b = m;
+    }
+    uint32_t c = a, d = hi;
+    while (c < d) {
+        const uint32_t m = (c + d) >> 1;
+        if (keys[m] <= key) c = m + 1; else d = m;
+    }
+    return c - a;
+}
+
 // One lane's group of up to VEC query slots; all 32 lanes of the warp call it together.
 template <typename K, int OUT, bool GATHER>
 __device__ __forceinline__ void probe_group(const uint64_t (&slot)[KeyVec<K>::N], const bool (&valid)[KeyVec<K>::N],
@@ -122,7 +144,7 @@ __device__ __forceinline__ void probe_group(const uint64_t (&slot)[KeyVec<K>::N]
                                             const uint32_t* __restrict__ vals, const uint32_t* __restrict__ offs,
                                             const Hasher& H, uint32_t n_keys, void* counts, const LongSink& L,
                                             const uint64_t* __restrict__ out_offs, uint32_t* out_vals,
-                                            uint64_t& acc) {
+                                            uint64_t& acc, uint32_t sorted_max) {
     constexpr int VEC = KeyVec<K>::N;
     const unsigned lane = lane_id();
     uint32_t lo[VEC], hi[VEC], cnt[VEC];
@@ -148,8 +170,14 @@ __device__ __forceinline__ void probe_group(const uint64_t (&slot)[KeyVec<K>::N]
     }
     if (!GATHER) {
 #pragma unroll
-        for (int j = 0; j < VEC; ++j)
+        for (int j = 0; j < VEC; ++j) {
             if (cls[j] == CLS_LANE) cnt[j] = lane_count(keys, lo[j], hi[j], qk[j]);
+            // sorted buckets (HG_SORTED_BUCKETS) of more keys: two binary searches
+            if (cls[j] > CLS_LANE && hi[j] - lo[j] <= sorted_max) {
+                cnt[j] = sorted_count(keys, lo[j], hi[j], qk[j]);
+                cls[j] = CLS_NONE;
+            }
+        }
         // long buckets: append to the work list (warp-aggregated); on overflow the warp walks it
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
@@ -213,7 +241,8 @@ template <typename K, int OUT, bool TOTAL, bool GATHER>
 __global__ void __launch_bounds__(PROBE_THREADS)
 k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, const K* __restrict__ keys,
         const uint32_t* __restrict__ vals, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
-        uint64_t* total, LongSink L, const uint64_t* __restrict__ out_offs, uint32_t* out_vals) {
+        uint64_t* total, LongSink L, const uint64_t* __restrict__ out_offs, uint32_t* out_vals,
+        uint32_t sorted_max) {
     constexpr int VEC = KeyVec<K>::N;
     const unsigned lane = lane_id();
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -233,7 +262,8 @@ k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, cons
             valid[j] = ok;
             qk[j] = ok ? kv.k[j] : (K)0;
         }
-        probe_group<K, OUT, GATHER>(slot, valid, qk, keys, vals, offs, H, n_keys, counts, L, out_offs, out_vals, acc);
+        probe_group<K, OUT, GATHER>(slot, valid, qk, keys, vals, offs, H, n_keys, counts, L, out_offs, out_vals, acc,
+                                    sorted_max);
     }
     if (gw == 0) {
         const uint64_t tail0 = head + nvec * VEC;
@@ -244,7 +274,8 @@ k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, cons
             slot[j] = lane < head ? lane : tail0 + (lane - head);
             qk[j] = valid[j] ? qs[slot[j]] : (K)0;
         }
-        probe_group<K, OUT, GATHER>(slot, valid, qk, keys, vals, offs, H, n_keys, counts, L, out_offs, out_vals, acc);
+        probe_group<K, OUT, GATHER>(slot, valid, qk, keys, vals, offs, H, n_keys, counts, L, out_offs, out_vals, acc,
+                                    sorted_max);
     }
     if (TOTAL) {
         const uint64_t s = block_sum(acc);
@@ -491,7 +522,9 @@ cudaError_t run_probe(const Table& t, const K* qs, uint64_t q, void* counts, uin
         if (need < g) g = (unsigned)(need < 1 ? 1 : need);
         launch_begin(GATHER ? "gather" : "probe", s);
         kern<<<g, PROBE_THREADS, 0, s>>>(qs, q, head, nvec, keys, t.values, t.offsets, t.H, (uint32_t)t.n, counts,
-                                         total, sink_of(L), out_offs, out_vals);
+                                         total, sink_of(L), out_offs, out_vals,
+                                         // a gather's two phases must agree on the long slots: both walk
+                                         (GATHER || OUT == OUT_U64) ? 0u : sorted_limit(t));
         launch_end(GATHER ? "gather" : "probe", s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -566,7 +599,7 @@ template <typename K, int OUT, bool TOTAL>
 __global__ void __launch_bounds__(BIN_PROBE_THREADS, BIN_PROBE_CTAS_PER_SM)
 k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, uint32_t nbins,
              const K* __restrict__ keys, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
-             uint64_t* total, LongSink L, uint32_t* work_ctr, uint32_t* err) {
+             uint64_t* total, LongSink L, uint32_t* work_ctr, uint32_t* err, uint32_t sorted_max) {
     constexpr uint32_t KVEC = 16 / sizeof(K);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -658,6 +691,10 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
             const uint32_t len = hi - lo;
             uint8_t cls = !ok ? CLS_NONE : len <= WALK_LANE ? CLS_LANE : len <= WALK_WARP ? CLS_WARP : CLS_LONG;
             uint32_t cnt = 0;
+            if (cls > CLS_LANE && len <= sorted_max) {  // a sorted bucket (HG_SORTED_BUCKETS)
+                cnt = sorted_count(kb, lo, hi, key);
+                cls = CLS_NONE;
+            }
             if (cls == CLS_LANE)
                 for (uint32_t x = lo; x < hi; ++x) cnt += (kb[x] == key);
             // long buckets to the list (warp-aggregated); on overflow the warp walks them
@@ -755,7 +792,8 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
             per_sm = 1;
         launch_begin("probe", s);
         kern<<<num_sms() * per_sm, BIN_PROBE_THREADS, smem, s>>>(qs, g.bin_start, g.nbins, keys, t.offsets, t.H,
-                                                                 (uint32_t)t.n, counts, total, sink_of(L), work_ctr, t.err);
+                                                                 (uint32_t)t.n, counts, total, sink_of(L), work_ctr, t.err,
+                                                                 sorted_limit(t));
         launch_end("probe", s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

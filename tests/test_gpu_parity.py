@@ -34,6 +34,19 @@ def _run_all(hg, keys, B, seed, queries, values=None, flags=0, check_gather=True
     return ref
 
 
+def _check_sorted(o, k, limit):
+    """Every bucket of at most `limit` keys is in ascending order."""
+    lens = np.diff(o.astype(np.int64))
+    if k.size < 2:
+        return
+    step_down = np.flatnonzero(k[1:] < k[:-1]) + 1        # positions where the order breaks
+    bucket_of_pos = np.searchsorted(o.astype(np.int64), step_down, side="right") - 1
+    starts = o.astype(np.int64)[bucket_of_pos]
+    inside = step_down > starts                          # not the first key of its bucket
+    bad = bucket_of_pos[inside]
+    assert np.all(lens[bad] > limit), "a sorted-size bucket is out of order"
+
+
 def _run_one(hg, ref, keys, B, seed, queries, values, flags, check_gather):
     dt = keys.dtype
     dk = to_dev(keys)
@@ -42,6 +55,8 @@ def _run_one(hg, ref, keys, B, seed, queries, values, flags, check_gather):
     with hg.hg_build(dk, B, seed, values=dv, flags=flags) as t:
         o, k, v = table_arrays(hg, t, dt)
         assert_same_table(o, k, v, ref)
+        if flags & hg.HG_SORTED_BUCKETS:
+            _check_sorted(o, k, 16384 if dt == np.uint32 else 8192)
         # counts and total in one call
         counts = torch.empty(queries.size, dtype=torch.int32, device="cuda")
         total = torch.empty(1, dtype=torch.int64, device="cuda")
@@ -274,19 +289,20 @@ def _probe_only(hg, keys, B, queries, values=None):
 def test_grouped_probe_zipf_u32_two_passes(hg):
     # table > 48 MB (not L2-resident): queries are grouped by table bin in two
     # partition passes, probed bin by bin, and the counts return to slot order
-    wl = W.zipf_large(n=(1 << 23) + 11, num_buckets=1 << 22, q=(1 << 21) + 3, M=1 << 18, salt=8)
-    _probe_only(hg, wl.keys, 1 << 22, wl.queries)
+    wl = W.zipf_large(n=(1 << 23) + 11, num_buckets=1 << 23, q=(1 << 21) + 3, M=1 << 18, salt=8)
+    _probe_only(hg, wl.keys, 1 << 23, wl.queries)
 
 
-def test_grouped_probe_one_pass(hg):
-    # 2^20 buckets = 128 bins: the grouping takes a single partition pass
+def test_large_table_few_bins(hg):
+    # 2^20 buckets = 128 bins, fewer than the probe's CTAs: the direct probe answers
+    # a table larger than L2 (grouping needs several bins per SM)
     wl = W.plain_uniform((1 << 24) + 5, (1 << 20) + 7, num_buckets=1 << 20, salt=12)
     _probe_only(hg, wl.keys, 1 << 20, wl.queries)
 
 
 def test_grouped_probe_u64(hg):
-    wl = W.join_kv(n=(1 << 22) + (1 << 20), num_buckets=(1 << 22) - 9, q=(1 << 21) + 1, salt=10)
-    _probe_only(hg, wl.keys, (1 << 22) - 9, wl.queries, values=wl.values)
+    wl = W.join_kv(n=(1 << 22) + (1 << 20), num_buckets=(1 << 23) - 9, q=(1 << 21) + 1, salt=10)
+    _probe_only(hg, wl.keys, (1 << 23) - 9, wl.queries, values=wl.values)
 
 
 @pytest.mark.parametrize("dup_log2", [0, 3, 6, 9, 12])
@@ -294,3 +310,26 @@ def test_duplicate_key_sweep(hg, dup_log2):
     """The duplicate-key experiment's inputs: every value about 2^d times, B = N / 2^d."""
     wl = W.duplicate_keys((1 << 16) + 5, dup_log2=dup_log2, q=(1 << 14) + 3, salt=dup_log2)
     _run_all(hg, wl.keys, wl.num_buckets, 0, wl.queries, check_gather=False)
+
+
+@pytest.mark.parametrize("case", ["zipf", "dup9", "one_bucket", "medium_buckets", "u64_values"])
+def test_sorted_buckets(hg, case):
+    """HG_SORTED_BUCKETS: same table contents and counts; buckets up to the limit ascending."""
+    if case == "zipf":
+        wl = W.zipf_large(n=1 << 20, num_buckets=1 << 19, q=1 << 17, M=1 << 14, salt=40)
+        _run_all(hg, wl.keys, 1 << 19, 0, wl.queries, flags=hg.HG_SORTED_BUCKETS | hg.HG_INDEX_VALUES)
+    elif case == "dup9":
+        wl = W.duplicate_keys((1 << 16) + 5, dup_log2=9, q=(1 << 14) + 3, salt=41)
+        _run_all(hg, wl.keys, wl.num_buckets, 0, wl.queries, flags=hg.HG_SORTED_BUCKETS)
+    elif case == "one_bucket":   # longer than the limit: left in build order, walked
+        wl = W.plain_uniform(100003, 20001, num_buckets=1, salt=42)
+        _run_all(hg, wl.keys, 1, 0, wl.queries, flags=hg.HG_SORTED_BUCKETS)
+    elif case == "medium_buckets":  # ~14,000 keys per bucket, bitonic-sorted in shared memory
+        rng = np.random.default_rng(43)
+        keys = rng.integers(0, 3000, size=100003, dtype=np.uint32)
+        keys[::11] = 0xFFFFFFFF  # the largest key value, equal to the sort's padding
+        queries = np.concatenate([keys[:5000], rng.integers(0, 1 << 32, size=3000, dtype=np.uint64).astype(np.uint32)])
+        _run_all(hg, keys, 7, 5, queries, flags=hg.HG_SORTED_BUCKETS | hg.HG_INDEX_VALUES)
+    else:
+        wl = W.join_kv(n=(1 << 17) + 3, num_buckets=1 << 12, q=(1 << 15) + 5, salt=44)
+        _run_all(hg, wl.keys, 1 << 12, 0, wl.queries, values=wl.values, flags=hg.HG_SORTED_BUCKETS)
