@@ -370,7 +370,6 @@ def run_ours(args, rank, world, local_rank):
         time.sleep(0.3)
         barrier()
         torch.cuda.synchronize(dev)
-        hg.hg_prof_enable(True)
         launches0 = hg.hg_launch_count()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -378,10 +377,25 @@ def run_ours(args, rank, world, local_rank):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         launches = hg.hg_launch_count() - launches0
-        hg.hg_prof_enable(False)
         barrier()
         ms = ev0.elapsed_time(ev1) / args.steps
+
+        # per-kernel times: a second timed run of the step with the query after the
+        # build on one stream, so that each kernel's events bracket only its own work
+        # (in the step above the query grouping overlaps the build)
+        k_steps = max(3, args.steps // 3)
+        hg.hg_prof_enable(True)
+        ev0.record(stream)
+        for _ in range(k_steps):
+            t = hg.hg_build(keys, B, 0, stream=stream)
+            hg.hg_query_count(t, queries, counts, total, stream=stream)
+            t.free(stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        hg.hg_prof_enable(False)
+        kernel_run_ms = ev0.elapsed_time(ev1) / k_steps
         prof = {name: hg.hg_prof_read(name) for name in hg.hg_prof_names()}
+        prof = {name: (n // k_steps * args.steps, tot_ms / k_steps * args.steps) for name, (n, tot_ms) in prof.items()}
 
         # end to end through the C ABI with host buffers: pinned inputs copied in,
         # counts and total copied out, inside the timed region
@@ -461,6 +475,9 @@ def run_ours(args, rank, world, local_rank):
                      "step_model_bytes": step_bytes,
                      "step_frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
         "kernels": per_kernel,
+        "kernel_timing": {"ms_per_step": kernel_run_ms,
+                          "how": "per-kernel CUDA events over a second timed run of the step with the query after "
+                                 "the build on one stream (launch counts and totals scaled to the main run's steps)"},
         "walk": walk,
         "gpu_launches": launches,
         "clocks": {k2: clocks[k2] for k2 in ("sm_mhz", "sm_max_mhz", "reasons")},
