@@ -42,8 +42,11 @@ def parse():
     p.add_argument("--cpu-sample-log2", type=int, default=27)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="zipf_large", choices=["zipf_large", "batched", "serving", "dupsweep"],
-                   help="zipf_large: the 2^28 build+probe step; batched: 4096 tables in one persistent launch; "
+    p.add_argument("--workload", default="zipf_large",
+                   choices=["zipf_large", "zipf_weighted", "batched", "serving", "dupsweep"],
+                   help="zipf_large: the 2^28 build+probe step; zipf_weighted: the same keys with hits drawn by "
+                        "the keys' own Zipf law (each value queried in proportion to its copies); "
+                        "batched: 4096 tables in one persistent launch; "
                         "serving: a Poisson stream of build and probe requests through the serving engine; "
                         "dupsweep: the duplicate-key experiment (each value 2^d times, B = N / 2^d)")
     p.add_argument("--sweep-log2n", type=int, default=26, help="dupsweep: log2 of keys (and queries)")
@@ -52,6 +55,9 @@ def parse():
                    help="zipf_large: plan = hg_query_plan_create on a second stream while the table builds, then "
                         "hg_query_count_plan; probe = hg_query_count after the build; intersect = "
                         "hg_query_count_intersect (HG(Q) + bucket intersections, the paper's query form)")
+    p.add_argument("--long-summary", default="auto", choices=["auto", "on", "off"],
+                   help="build with HG_LONG_SUMMARY (buckets of more than 8192 keys condensed to their distinct "
+                        "keys); auto = on for zipf_weighted, off for zipf_large")
     p.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / the plain path's capacity")
     p.add_argument("--budget-gb", type=float, default=100.0, help="serving: device-memory budget for tables")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
@@ -59,9 +65,26 @@ def parse():
     return p.parse_args()
 
 
-def workload_desc(log2n):
+def workload_desc(log2n, weighted=False):
+    if weighted:
+        return (f"zipf_weighted: N=2^{log2n} uint32 keys Zipf(s=1) over 2^24 values, B=2^{log2n - 1} buckets, "
+                f"murmur3-fmix32 seed 0, Q=2^{log2n} queries 70% hits (ranks Zipf(s=1) like the keys)")
     return (f"zipf_large: N=2^{log2n} uint32 keys Zipf(s=1) over 2^24 values, B=2^{log2n - 1} buckets, "
             f"murmur3-fmix32 seed 0, Q=2^{log2n} queries 70% hits (ranks uniform over the 2^24 values)")
+
+
+def use_summary(args):
+    if args.long_summary == "auto":
+        return args.workload == "zipf_weighted"
+    return args.long_summary == "on"
+
+
+def cpu_sample_log2(args):
+    # the oracle's walk is quadratic in the copies of a Zipf-weighted query's value:
+    # its sample is smaller so that it still ends in seconds
+    if args.workload == "zipf_weighted":
+        return min(args.cpu_sample_log2, 21)
+    return args.cpu_sample_log2
 
 
 def max_over_ranks(values, dist, device):
@@ -80,9 +103,10 @@ def aggregate_gkeys(world, keys_per_rank, ms):
     return world * keys_per_rank / (ms * 1e-3) / 1e9
 
 
-def make_workload(log2n, salt):
+def make_workload(log2n, salt, weighted=False):
     import workloads as W
-    return W.zipf_large(n=1 << log2n, num_buckets=1 << (log2n - 1), q=1 << log2n, M=1 << 24, hit=0.7, salt=salt)
+    make = W.zipf_weighted if weighted else W.zipf_large
+    return make(n=1 << log2n, num_buckets=1 << (log2n - 1), q=1 << log2n, M=1 << 24, hit=0.7, salt=salt)
 
 
 class ClockSampler:
@@ -222,20 +246,21 @@ def cpu_oracle_sample(wl, log2s):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = make_workload(args.log2n, 0)
+    wl = make_workload(args.log2n, 0, args.workload == "zipf_weighted")
     times = []
     res = None
     for _ in range(args.warmup):
-        cpu_oracle_sample(wl, args.cpu_sample_log2 - 2)
+        cpu_oracle_sample(wl, cpu_sample_log2(args) - 2)
     for _ in range(args.steps):
-        res = cpu_oracle_sample(wl, args.cpu_sample_log2 - 2)
+        res = cpu_oracle_sample(wl, cpu_sample_log2(args) - 2)
         times.append(res["value"])
     v = statistics.median(times)
     res["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": workload_desc(args.log2n), "reference": "CPU oracle (oracle/hg_oracle.c)"},
+            "config": {"workload": workload_desc(args.log2n, args.workload == "zipf_weighted"),
+                       "reference": "CPU oracle (oracle/hg_oracle.c)"},
             "cpu_baseline": res, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -321,7 +346,9 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    wl = make_workload(args.log2n, rank)
+    weighted = args.workload == "zipf_weighted"
+    wl = make_workload(args.log2n, rank, weighted)
+    flags = hg.HG_LONG_SUMMARY if use_summary(args) else 0
     N, Q, B = wl.keys.size, wl.queries.size, wl.num_buckets
     keys = torch.from_numpy(wl.keys.view(np.int32)).to(dev)
     queries = torch.from_numpy(wl.queries.view(np.int32)).to(dev)
@@ -340,7 +367,7 @@ def run_ours(args, rank, world, local_rank):
             # the queries are grouped on a second stream while the table builds: the
             # plan needs only the table's shape, which hg_build fixes on return
             forked.record(stream)                 # inputs are ready here
-            t = hg.hg_build(k, B, 0, stream=stream)
+            t = hg.hg_build(k, B, 0, flags=flags, stream=stream)
             side.wait_event(forked)
             plan = hg.hg_query_plan_create(t, qs, stream=side)
             joined.record(side)
@@ -348,7 +375,7 @@ def run_ours(args, rank, world, local_rank):
             hg.hg_query_count_plan(t, plan, c, tot, stream=stream)
             plan.free(stream)
         else:
-            t = hg.hg_build(k, B, 0, stream=stream)
+            t = hg.hg_build(k, B, 0, flags=flags, stream=stream)
             query(t, qs, c, tot, stream=stream)
         t.free(stream)
 
@@ -360,7 +387,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
 
     # byte model inputs (outside the timed region)
-    with hg.hg_build(keys, B, 0, stream=stream) as t:
+    with hg.hg_build(keys, B, 0, flags=flags, stream=stream) as t:
         walk = hg.hg_probe_stats(t, queries, stream=stream)
     torch.cuda.synchronize(dev)
 
@@ -387,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
         hg.hg_prof_enable(True)
         ev0.record(stream)
         for _ in range(k_steps):
-            t = hg.hg_build(keys, B, 0, stream=stream)
+            t = hg.hg_build(keys, B, 0, flags=flags, stream=stream)
             hg.hg_query_count(t, queries, counts, total, stream=stream)
             t.free(stream)
         ev1.record(stream)
@@ -445,7 +472,13 @@ def run_ours(args, rank, world, local_rank):
         model["chunk_count"] = k * N                   # (same for the query side: Q = N here)
         model["q_reverse"] = 12 * Q                    # ranks, grouped counts in, counts out
     # the method's own byte model for the whole step (build + probe; offsets 4 B)
-    step_model = (3 * k) * N + 16 * B + (k + 12) * Q + k * W
+    if flags:
+        # summarised long buckets (HG_LONG_SUMMARY): each of their queries reads the
+        # bucket's summary (a few words) instead of walking the bucket
+        walk_bytes = k * (W - WL) + 8 * walk["long_slots"]
+    else:
+        walk_bytes = k * W
+    step_model = (3 * k) * N + 16 * B + (k + 12) * Q + walk_bytes
     per_kernel = {}
     for name, (n_launch, tot_ms) in prof.items():
         if n_launch:
@@ -463,7 +496,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": workload_desc(args.log2n), "parallelism": f"replicas{world}",
+        "config": {"workload": workload_desc(args.log2n, weighted), "parallelism": f"replicas{world}",
+                   "build_flags": "HG_LONG_SUMMARY" if flags else "none",
                    "l2": "inputs exceed L2 (2 GiB read per step); no flush",
                    "step": {"plan": "hg_build, with hg_query_plan_create on a second stream, then "
                                     "hg_query_count_plan(counts, total) + hg_free",
@@ -489,7 +523,7 @@ def run_ours(args, rank, world, local_rank):
                        "ms_per_step": e2e["ms"], "total_equals_sum_of_counts": e2e["check"],
                        "pipelining": "copies on their own streams, two device buffer sets alternating"}
     if world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_sample(wl, args.cpu_sample_log2)
+        line["cpu_baseline"] = cpu_oracle_sample(wl, cpu_sample_log2(args))
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

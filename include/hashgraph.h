@@ -8,7 +8,7 @@
  * keys that hash to bucket i are keys[offset[i]] .. keys[offset[i+1] - 1].
  * Building it is Algorithm 1 (hash, count per bucket, prefix sum, scatter);
  * a query hashes the probe key and walks its bucket (Sec. 3.3), counting
- * every equal key (duplicates included, Sec. 5.5).
+ * every equal key (duplicates included, Sec. 5.4).
  *
  * Conventions shared by every call:
  *  - Pointers named d_* are CUDA device memory on the calling thread's
@@ -63,8 +63,15 @@ typedef enum {
 #define HG_SORTED_BUCKETS 0x8u /* after the build, sort the keys (with their values) inside every bucket of at
                                   most 16384 keys (8192 for 64-bit keys), so that counting a key in such a
                                   bucket takes two binary searches instead of a walk whose length grows with
-                                  the copies of each key (the duplicate-key regime, Sec. 5.5); offsets and
+                                  the copies of each key (the duplicate-key regime, Sec. 5.4); offsets and
                                   bucket contents are unchanged, only their order inside a bucket is fixed */
+#define HG_LONG_SUMMARY 0x10u /* after the build, condense every bucket of more than 8192 keys into its
+                                 distinct keys and their multiplicities (at most 64, ascending by key);
+                                 hg_query_count and hg_join_count then answer a query on such a bucket by a
+                                 binary search of that list instead of a walk over all its copies (the
+                                 duplicate-key regime, Sec. 5.4).  A bucket with more distinct keys keeps no
+                                 list and is walked as before.  Extra device memory: at most n / 14 bytes
+                                 (u32 keys) or n / 10 bytes (u64 keys) */
 
 typedef struct {
     uint32_t key_bytes;   /* 4 or 8 */
@@ -98,7 +105,7 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const void* d_value
 
 /*
  * hg_query_count -- for each query slot i, d_counts[i] = number of table keys
- * equal to d_queries[i] (bucket walk, Sec. 3.3; duplicates counted, Sec. 5.5).
+ * equal to d_queries[i] (bucket walk, Sec. 3.3; duplicates counted, Sec. 5.4).
  *   d_queries  q keys of the table's key width
  *   d_counts   q uint32_t outputs (may be NULL if d_total is given)
  *   d_total    optional single uint64_t: receives the sum of the counts (the
@@ -180,6 +187,25 @@ hg_status hg_sync(const hg_table* t, hg_stream_t s);
  */
 hg_status hg_table_view(const hg_table* t, const void** d_offsets, const void** d_keys,
                         const void** d_values, uint64_t* n, uint64_t* num_buckets);
+
+/*
+ * hg_long_summary_view -- borrow a HG_LONG_SUMMARY table's bucket summaries
+ * (valid until hg_free; all device arrays, filled once the build's stream
+ * has reached the end of hg_build):
+ *   d_n_long   uint32_t[1]: number of summarised buckets L (buckets of more
+ *              than 8192 keys; L <= *cap)
+ *   d_bucket   uint32_t[*cap]: bucket id of summary l, for l < L (any order)
+ *   d_len      uint32_t[*cap]: entries of summary l, or 0xFFFFFFFF when the
+ *              bucket has more than *slots distinct keys (no summary)
+ *   d_keys     key_bytes-wide keys, summary l at [l * *slots, l * *slots + len),
+ *              strictly ascending
+ *   d_counts   uint32_t, the multiplicity of each of those keys in the bucket
+ * A table built without HG_LONG_SUMMARY, or with n <= 8192, has *cap = 0 and
+ * NULL arrays.  Any output pointer may be NULL.
+ */
+hg_status hg_long_summary_view(const hg_table* t, const uint32_t** d_n_long, const uint32_t** d_bucket,
+                               const uint32_t** d_len, const void** d_keys, const uint32_t** d_counts,
+                               uint32_t* cap, uint32_t* slots);
 
 /*
  * hg_probe_stats -- byte-model helper for diagnostics (not part of a query):

@@ -19,7 +19,7 @@
  *   - inside a bucket the oracle keeps input order (its scatter is a
  *     sequential loop); the paper's atomics leave that order free.
  *   - a query slot's count is the number of input keys equal to it
- *     (Sec. 5.5, query performance counts every occurrence).
+ *     (Sec. 5.4, query performance counts every occurrence).
  *
  * Parity pins: none of these functions is trusted on its own; the
  * "not gpu" tests check them against published MurmurHash3 vectors, brute

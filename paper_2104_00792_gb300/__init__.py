@@ -39,6 +39,7 @@ HG_INDEX_VALUES = 0x1
 HG_PLAIN_BUILD = 0x2
 HG_PARTITION_BUILD = 0x4
 HG_SORTED_BUCKETS = 0x8
+HG_LONG_SUMMARY = 0x10
 
 
 class hg_config(ctypes.Structure):
@@ -65,6 +66,8 @@ lib.hg_sync.argtypes = [_vp, _vp]
 lib.hg_table_view.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                               ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
 lib.hg_probe_stats.argtypes = [_vp, _vp, _u64, _vp, _vp]
+lib.hg_long_summary_view.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 5 + [ctypes.POINTER(ctypes.c_uint32)] * 2
+lib.hg_long_summary_view.restype = ctypes.c_int
 lib.hg_selftest_bounded_wait.argtypes = [_vp]
 lib.hg_selftest_bounded_wait.restype = ctypes.c_int
 lib.hg_launch_count.restype = _u64
@@ -265,6 +268,27 @@ def hg_table_view(table: Table):
     if v.value:
         vals = torch.as_tensor(_DeviceArray(v.value, n.value, "<i4"), device=dev)
     return offs, keys, vals
+
+
+def hg_long_summary_view(table: Table):
+    """A HG_LONG_SUMMARY table's bucket summaries as zero-copy CUDA tensors:
+    dict(n_long int32[1], bucket int32[cap], len int32[cap], keys (cap * slots),
+    counts int32[cap * slots], cap, slots), or None when the table has none."""
+    ptrs = [_vp() for _ in range(5)]
+    cap, slots = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib.hg_long_summary_view(table.handle, *[ctypes.byref(x) for x in ptrs], ctypes.byref(cap),
+                                    ctypes.byref(slots)))
+    if cap.value == 0:
+        return None
+    dev = torch.device("cuda", torch.cuda.current_device())
+    c, sl = cap.value, slots.value
+
+    def arr(p, n, typestr):
+        return torch.as_tensor(_DeviceArray(p.value, n, typestr), device=dev)
+
+    return {"n_long": arr(ptrs[0], 1, "<i4"), "bucket": arr(ptrs[1], c, "<i4"), "len": arr(ptrs[2], c, "<i4"),
+            "keys": arr(ptrs[3], c * sl, "<i4" if table.key_bytes == 4 else "<i8"),
+            "counts": arr(ptrs[4], c * sl, "<i4"), "cap": c, "slots": sl}
 
 
 def hg_probe_stats(table: Table, queries: torch.Tensor, stream=None) -> dict:

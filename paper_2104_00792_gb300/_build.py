@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libhashgraph.so")
 OBJDIR = os.path.join(HERE, "_build")
 
 SOURCES = ["hg_api.cu", "hg_scan.cu", "hg_build.cu", "hg_partition.cu", "hg_probe.cu", "hg_noalloc.cu", "hg_batch.cu",
-           "hg_serve.cu", "hg_sort.cu"]
+           "hg_serve.cu", "hg_sort.cu", "hg_summary.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

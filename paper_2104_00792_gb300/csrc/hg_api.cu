@@ -42,7 +42,8 @@ std::atomic<uint64_t> g_launches{0};
 // ---- per-kernel event timing (diagnostics) ----
 const char* const kKernelNames[] = {"hist", "scan", "scatter", "probe", "long_prep", "long", "gather",
                                     "long_gather", "walk_stats", "part_hist", "part_plan", "chunk_scan", "chunk_count", "part_scatter", "huge_count",
-                                    "huge_scan", "bin_build", "q_part_count", "q_partition", "q_reverse", "batch", "probe_multi", "scatter_counts", "sort_buckets"};
+                                    "huge_scan", "bin_build", "q_part_count", "q_partition", "q_reverse", "batch", "probe_multi", "scatter_counts", "sort_buckets",
+                                    "sum_find", "sum_plan", "sum_count", "sum_finish"};
 struct ProfRecord {
     const char* name;
     cudaEvent_t start, stop;
@@ -177,6 +178,7 @@ void free_table(Table* t, cudaStream_t s) {
     dev_free(t->keys, s);
     dev_free(t->values, s);
     dev_free(t->err, s);
+    dev_free(t->sum_mem, s);
     delete t;
 }
 
@@ -201,7 +203,7 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const void* d_value
         return fail(HG_ERR_INVALID_ARG, "num_buckets = %llu, must be in [1, 2^31]",
                     (unsigned long long)cfg->num_buckets);
     if (n >= (1ull << 32)) return fail(HG_ERR_INVALID_ARG, "n = %llu must be < 2^32", (unsigned long long)n);
-    const uint32_t known = HG_INDEX_VALUES | HG_PLAIN_BUILD | HG_PARTITION_BUILD | HG_SORTED_BUCKETS;
+    const uint32_t known = HG_INDEX_VALUES | HG_PLAIN_BUILD | HG_PARTITION_BUILD | HG_SORTED_BUCKETS | HG_LONG_SUMMARY;
     if (cfg->flags & ~known) return fail(HG_ERR_INVALID_ARG, "unknown flags 0x%x", cfg->flags & ~known);
     if ((cfg->flags & HG_PLAIN_BUILD) && (cfg->flags & HG_PARTITION_BUILD))
         return fail(HG_ERR_INVALID_ARG, "HG_PLAIN_BUILD and HG_PARTITION_BUILD are exclusive");
@@ -239,6 +241,7 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const void* d_value
     }
     e = build_table(*t, d_keys, d_values, st);
     if (e == cudaSuccess && (cfg->flags & HG_SORTED_BUCKETS)) e = sort_buckets(*t, st);
+    if (e == cudaSuccess && (cfg->flags & HG_LONG_SUMMARY)) e = summarize_long_buckets(*t, st);
     if (e != cudaSuccess) {
         hg_status r = cuda_fail(e, "hg_build");
         free_table(t, st);
@@ -404,6 +407,21 @@ hg_status hg_table_view(const hg_table* ht, const void** d_offsets, const void**
     if (d_values) *d_values = t->values;
     if (n) *n = t->n;
     if (num_buckets) *num_buckets = t->B;
+    return HG_OK;
+}
+
+hg_status hg_long_summary_view(const hg_table* ht, const uint32_t** d_n_long, const uint32_t** d_bucket,
+                               const uint32_t** d_len, const void** d_keys, const uint32_t** d_counts,
+                               uint32_t* cap, uint32_t* slots) {
+    const Table* t = reinterpret_cast<const Table*>(ht);
+    if (!t) return fail(HG_ERR_INVALID_ARG, "table is NULL");
+    if (d_n_long) *d_n_long = t->sum_n_long;
+    if (d_bucket) *d_bucket = t->sum_bucket;
+    if (d_len) *d_len = t->sum.len;
+    if (d_keys) *d_keys = t->sum.keys;
+    if (d_counts) *d_counts = t->sum.cnt;
+    if (cap) *cap = t->sum_cap;
+    if (slots) *slots = SUM_SLOTS;
     return HG_OK;
 }
 

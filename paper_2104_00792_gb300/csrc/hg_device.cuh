@@ -148,4 +148,36 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Orders earlier generic-proxy accesses of shared memory before later async-proxy (bulk copy) ones.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Slot of bucket b in a long-bucket summary map (linear probing from here).
+__device__ __forceinline__ uint32_t summary_slot(uint32_t b, uint32_t mask) { return fmix32(b ^ 0x2c1b3c6du) & mask; }
+
+// Count of `key` in long bucket b from its summary (HG_LONG_SUMMARY): false
+// when the bucket has no summary (too many distinct keys, or none was made),
+// so that the caller walks it instead.
+template <typename K>
+__device__ __forceinline__ bool summary_count(const LongSummary& S, uint32_t b, K key, uint32_t& cnt) {
+    uint32_t h = summary_slot(b, S.map_mask);
+    uint32_t l = SUM_OVERFLOW;
+    for (uint32_t probe = 0; probe <= S.map_mask; ++probe) {
+        const unsigned long long w = __ldg(S.map + h);
+        if (w == ~0ull) return false;
+        if ((uint32_t)w == b) {
+            l = (uint32_t)(w >> 32);
+            break;
+        }
+        h = (h + 1) & S.map_mask;
+    }
+    if (l == SUM_OVERFLOW) return false;
+    const uint32_t n = __ldg(S.len + l);
+    if (n > SUM_SLOTS) return false;
+    const K* k = static_cast<const K*>(S.keys) + (size_t)l * SUM_SLOTS;
+    uint32_t a = 0, z = n;  // first entry >= key
+    while (a < z) {
+        const uint32_t m = (a + z) >> 1;
+        if (__ldg(k + m) < key) a = m + 1; else z = m;
+    }
+    cnt = (a < n && __ldg(k + a) == key) ? __ldg(S.cnt + (size_t)l * SUM_SLOTS + a) : 0u;
+    return true;
+}
+
 }  // namespace hg

@@ -32,6 +32,19 @@ enum : uint32_t { MODE_POW2 = 0, MODE_FAST32 = 1, MODE_DIV64 = 2 };
 
 Hasher make_hasher(uint32_t key_bytes, uint64_t B, uint64_t seed);
 
+// Long-bucket summaries (HG_LONG_SUMMARY): every bucket of more than
+// SUM_MIN_LEN keys as its distinct keys (ascending) with their multiplicities.
+constexpr uint32_t SUM_MIN_LEN = 8192;        // equals the probe's warp-walk limit
+constexpr uint32_t SUM_SLOTS = 64;            // entries per bucket summary
+constexpr uint32_t SUM_OVERFLOW = 0xFFFFFFFFu;  // summary length of a bucket with more distinct keys
+struct LongSummary {
+    const unsigned long long* map = nullptr;  // (l << 32 | bucket), all ones = empty; null: no summaries
+    uint32_t map_mask = 0;
+    const void* keys = nullptr;     // [cap * SUM_SLOTS]: summary l at l * SUM_SLOTS
+    const uint32_t* cnt = nullptr;  // [cap * SUM_SLOTS]
+    const uint32_t* len = nullptr;  // [cap]: entries, or SUM_OVERFLOW
+};
+
 struct Table {
     uint32_t key_bytes = 4;
     uint32_t has_values = 0;  // values array present (user values or input indices)
@@ -45,6 +58,11 @@ struct Table {
     void* keys = nullptr;         // n
     uint32_t* values = nullptr;   // n or null
     uint32_t* err = nullptr;      // device error word
+    LongSummary sum{};            // HG_LONG_SUMMARY
+    void* sum_mem = nullptr;
+    uint32_t sum_cap = 0;
+    const uint32_t* sum_n_long = nullptr;
+    const uint32_t* sum_bucket = nullptr;
 };
 
 // Sets the message hg_last_error() returns on the calling thread.
@@ -70,6 +88,9 @@ cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values
 uint32_t sorted_bucket_max(uint32_t key_bytes);
 cudaError_t sort_buckets(Table& t, cudaStream_t s);
 
+// HG_LONG_SUMMARY: fills t.sum (allocating t.sum_mem); run after the build.
+cudaError_t summarize_long_buckets(Table& t, cudaStream_t s);
+
 // Queries grouped by the table's bins (ranges of 8192 buckets), so that a
 // bin's offsets and keys stay in L1 while its queries are probed; the counts,
 // produced in grouped order, go back to slot order through reverse passes.
@@ -81,12 +102,25 @@ struct ChunkMap {
     const uint32_t* bin_start;
     const uint32_t* seg_chunk_start;  // [nseg + 1], segmented only
 };
+// Work items of the grouped probe: items [0, *huge_chunks) are slices of
+// huge_chunk queries of the bins with the most queries (huge bin e owns items
+// from huge_chunk_start[e]); the next *n_work items are whole bins, work[i].
+struct BinWork {
+    const uint32_t* n_huge = nullptr;  // device scalars, written by the grouping
+    const uint32_t* huge_chunks = nullptr;
+    const uint32_t* n_work = nullptr;
+    const uint32_t* huge_bin = nullptr;
+    const uint32_t* huge_chunk_start = nullptr;
+    const uint32_t* work = nullptr;
+    uint32_t huge_chunk = 0;
+};
 struct GroupedQueries {
     void* mem = nullptr;
     bool two = false;
     void* q_grouped = nullptr;  // queries in bin order (padded to a multiple of 4 elements)
     const uint32_t* bin_start = nullptr;  // [nbins + 1]: bin p's queries are q_grouped[bin_start[p] ..)
     uint32_t nbins = 0;
+    BinWork items{};
     // reverse-pass records (opaque to callers)
     ChunkMap cm_a{}, cm_b{};
     uint32_t nch_a = 0, nch_b_max = 0;

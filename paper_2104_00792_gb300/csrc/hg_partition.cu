@@ -1244,7 +1244,9 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
     }
     if (e == cudaSuccess) {
         launch_begin("part_plan", s);
-        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, nq, 0xffffffffu, bin_start, seg,
+        // bins of many queries first in the probe's work list; the bins with the
+        // most (huge bins) are cut into HUGE_CHUNK-query work items
+        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, nq, 1u << 16, bin_start, seg,
                                        reinterpret_cast<uint32_t*>(base + o_work),
                                        reinterpret_cast<uint32_t*>(base + o_hbin),
                                        reinterpret_cast<uint32_t*>(base + o_hcs), plan, nullptr, B);
@@ -1292,6 +1294,13 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
     g->nch_a = nch_a;
     g->nch_b_max = nch_b_max;
     g->plan = plan;
+    g->items.n_huge = &plan->n_huge;
+    g->items.huge_chunks = &plan->huge_chunks;
+    g->items.n_work = &plan->n_work;
+    g->items.huge_bin = reinterpret_cast<const uint32_t*>(base + o_hbin);
+    g->items.huge_chunk_start = reinterpret_cast<const uint32_t*>(base + o_hcs);
+    g->items.work = reinterpret_cast<const uint32_t*>(base + o_work);
+    g->items.huge_chunk = HUGE_CHUNK;
     g->dr_a = dr_a;
     g->dr_b = dr_b;
     g->lb_a = lb_a;

@@ -1,6 +1,6 @@
 // HashGraph query (Sec. 3.3): hash the probe key, read offset[b] and
 // offset[b + 1], walk keys[offset[b] .. offset[b + 1]) and count (or gather
-// the values of) every key equal to the probe, duplicates included (Sec. 5.5).
+// the values of) every key equal to the probe, duplicates included (Sec. 5.4).
 //
 // Buckets are walked by one of three workers, chosen by the bucket's length:
 //   <= WALK_LANE  keys : the query's own lane walks it;
@@ -144,7 +144,7 @@ __device__ __forceinline__ void probe_group(const uint64_t (&slot)[KeyVec<K>::N]
                                             const uint32_t* __restrict__ vals, const uint32_t* __restrict__ offs,
                                             const Hasher& H, uint32_t n_keys, void* counts, const LongSink& L,
                                             const uint64_t* __restrict__ out_offs, uint32_t* out_vals,
-                                            uint64_t& acc, uint32_t sorted_max) {
+                                            uint64_t& acc, uint32_t sorted_max, const LongSummary& S) {
     constexpr int VEC = KeyVec<K>::N;
     const unsigned lane = lane_id();
     uint32_t lo[VEC], hi[VEC], cnt[VEC];
@@ -176,6 +176,14 @@ __device__ __forceinline__ void probe_group(const uint64_t (&slot)[KeyVec<K>::N]
             if (cls[j] > CLS_LANE && hi[j] - lo[j] <= sorted_max) {
                 cnt[j] = sorted_count(keys, lo[j], hi[j], qk[j]);
                 cls[j] = CLS_NONE;
+            }
+            // summarised long buckets (HG_LONG_SUMMARY): a binary search of their distinct keys
+            if (cls[j] == CLS_LONG && S.map) {
+                uint32_t c = 0;
+                if (summary_count(S, bucket_of(qk[j], H), qk[j], c)) {
+                    cnt[j] = c;
+                    cls[j] = CLS_NONE;
+                }
             }
         }
         // long buckets: append to the work list (warp-aggregated); on overflow the warp walks it
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(PROBE_THREADS)
 k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, const K* __restrict__ keys,
         const uint32_t* __restrict__ vals, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
         uint64_t* total, LongSink L, const uint64_t* __restrict__ out_offs, uint32_t* out_vals,
-        uint32_t sorted_max) {
+        uint32_t sorted_max, LongSummary S) {
     constexpr int VEC = KeyVec<K>::N;
     const unsigned lane = lane_id();
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -263,7 +271,7 @@ k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, cons
             qk[j] = ok ? kv.k[j] : (K)0;
         }
         probe_group<K, OUT, GATHER>(slot, valid, qk, keys, vals, offs, H, n_keys, counts, L, out_offs, out_vals, acc,
-                                    sorted_max);
+                                    sorted_max, S);
     }
     if (gw == 0) {
         const uint64_t tail0 = head + nvec * VEC;
@@ -275,7 +283,7 @@ k_probe(const K* __restrict__ qs, uint64_t q, uint64_t head, uint64_t nvec, cons
             qk[j] = valid[j] ? qs[slot[j]] : (K)0;
         }
         probe_group<K, OUT, GATHER>(slot, valid, qk, keys, vals, offs, H, n_keys, counts, L, out_offs, out_vals, acc,
-                                    sorted_max);
+                                    sorted_max, S);
     }
     if (TOTAL) {
         const uint64_t s = block_sum(acc);
@@ -524,7 +532,8 @@ cudaError_t run_probe(const Table& t, const K* qs, uint64_t q, void* counts, uin
         kern<<<g, PROBE_THREADS, 0, s>>>(qs, q, head, nvec, keys, t.values, t.offsets, t.H, (uint32_t)t.n, counts,
                                          total, sink_of(L), out_offs, out_vals,
                                          // a gather's two phases must agree on the long slots: both walk
-                                         (GATHER || OUT == OUT_U64) ? 0u : sorted_limit(t));
+                                         (GATHER || OUT == OUT_U64) ? 0u : sorted_limit(t),
+                                         (GATHER || OUT == OUT_U64) ? LongSummary{} : t.sum);
         launch_end(GATHER ? "gather" : "probe", s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -597,13 +606,13 @@ constexpr unsigned long long CACHE_EMPTY = ~0ull;  // a count never reaches 2^32
 
 template <typename K, int OUT, bool TOTAL>
 __global__ void __launch_bounds__(BIN_PROBE_THREADS, BIN_PROBE_CTAS_PER_SM)
-k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, uint32_t nbins,
+k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, BinWork W,
              const K* __restrict__ keys, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
-             uint64_t* total, LongSink L, uint32_t* work_ctr, uint32_t* err, uint32_t sorted_max) {
+             uint64_t* total, LongSink L, uint32_t* work_ctr, uint32_t* err, uint32_t sorted_max, LongSummary S) {
     constexpr uint32_t KVEC = 16 / sizeof(K);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ uint32_t s_bin[2], s_k0[2], s_klo[2], s_staged[2];
+    __shared__ uint32_t s_bin[2], s_k0[2], s_klo[2], s_staged[2], s_q0[2], s_q1[2];
     static_assert(BIN_BUFFERS == 1 || BIN_BUFFERS == 2, "one or two bin buffers");
     constexpr bool CACHE = sizeof(K) == 4;
     __shared__ unsigned long long s_cache[CACHE ? CACHE_SLOTS : 1];  // (count << 32 | key)
@@ -611,6 +620,8 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
     const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint64_t B = H.B;
     uint64_t acc = 0;
+    const uint32_t n_huge = *W.n_huge, huge_items = *W.huge_chunks;
+    const uint32_t n_items = huge_items + *W.n_work;
 
     if (threadIdx.x == 0) {
         mbar_init(&s_bar[0], 1);
@@ -618,11 +629,31 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // thread 0: claim the next bin and start its copies into buffer b
+    // thread 0: claim the next work item (a slice of a huge bin's queries, or a
+    // whole bin) and start the copies of its bin into buffer b
     auto issue = [&](int b) {
-        const uint32_t p = atomicAdd(work_ctr, 1u);
+        const uint32_t item = atomicAdd(work_ctr, 1u);
+        if (item >= n_items) {
+            s_bin[b] = ~0u;
+            return;
+        }
+        uint32_t p;
+        if (item < huge_items) {
+            uint32_t lo = 0, hi = n_huge;  // last huge bin e with huge_chunk_start[e] <= item
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (W.huge_chunk_start[mid] <= item) lo = mid; else hi = mid;
+            }
+            p = W.huge_bin[lo];
+            const uint32_t c0 = qbin_start[p] + (item - W.huge_chunk_start[lo]) * W.huge_chunk;
+            s_q0[b] = c0;
+            s_q1[b] = min(qbin_start[p + 1], c0 + W.huge_chunk);
+        } else {
+            p = W.work[item - huge_items];
+            s_q0[b] = qbin_start[p];
+            s_q1[b] = qbin_start[p + 1];
+        }
         s_bin[b] = p;
-        if (p >= nbins) return;
         const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
         const uint32_t nb = (uint32_t)min((uint64_t)BIN_BUCKETS, B - b0);
         const uint32_t k0 = min(__ldg(offs + b0), n_keys);
@@ -652,7 +683,7 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
             for (uint32_t t = threadIdx.x; t < CACHE_SLOTS; t += blockDim.x) s_cache[t] = CACHE_EMPTY;
         __syncthreads();
         const uint32_t p = s_bin[cur];
-        if (p >= nbins) break;
+        if (p == ~0u) break;
         {
             const uint32_t ph = cur ? phase1 : phase0;
             uint32_t polls = 0;
@@ -668,7 +699,7 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
         const K* kb = staged ? reinterpret_cast<const K*>(smem + (size_t)cur * BIN_BUF_BYTES + BIN_OFF_BYTES) +
                                    (k0 - s_klo[cur])
                              : keys + k0;  // keys of the bin, indexed from k0
-        const uint32_t q0 = qbin_start[p], q1 = qbin_start[p + 1];
+        const uint32_t q0 = s_q0[cur], q1 = s_q1[cur];
         const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
         const uint32_t nb = (uint32_t)min((uint64_t)BIN_BUCKETS, B - b0);
         // each warp answers 32 queries at a time; the next 32 are loaded meanwhile
@@ -697,21 +728,8 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
             }
             if (cls == CLS_LANE)
                 for (uint32_t x = lo; x < hi; ++x) cnt += (kb[x] == key);
-            // long buckets to the list (warp-aggregated); on overflow the warp walks them
-            const unsigned lm = __ballot_sync(FULL_MASK, cls == CLS_LONG);
-            if (lm) {
-                const int leader = __ffs(lm) - 1;
-                uint32_t base = 0;
-                if ((int)lane == leader) base = atomicAdd(L.n, (uint32_t)__popc(lm));
-                base = __shfl_sync(FULL_MASK, base, leader);
-                if (cls == CLS_LONG) {
-                    const uint32_t pos = base + __popc(lm & lanemask_lt());
-                    if (pos < L.cap) L.slot[pos] = i;
-                    else cls = CLS_WARP;
-                }
-            }
-            // a key already walked in this bin takes its count from the table
-            if (CACHE && cls == CLS_WARP) {
+            // a key already counted in this bin takes its count from the table
+            if (CACHE && cls >= CLS_WARP) {
                 uint32_t sl = j & (CACHE_SLOTS - 1);
                 for (uint32_t t = 0; t < CACHE_PROBES; ++t) {
                     const unsigned long long w = s_cache[sl];
@@ -722,6 +740,25 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
                         break;
                     }
                     sl = (sl + 1) & (CACHE_SLOTS - 1);
+                }
+            }
+            // summarised long buckets (HG_LONG_SUMMARY): a binary search of their distinct keys
+            bool summarised = false;
+            if (cls == CLS_LONG && S.map) {
+                summarised = summary_count(S, (uint32_t)b0 + j, key, cnt);
+                if (summarised) cls = CLS_NONE;
+            }
+            // other long buckets to the list (warp-aggregated); on overflow the warp walks them
+            const unsigned lm = __ballot_sync(FULL_MASK, cls == CLS_LONG);
+            if (lm) {
+                const int leader = __ffs(lm) - 1;
+                uint32_t base = 0;
+                if ((int)lane == leader) base = atomicAdd(L.n, (uint32_t)__popc(lm));
+                base = __shfl_sync(FULL_MASK, base, leader);
+                if (cls == CLS_LONG) {
+                    const uint32_t pos = base + __popc(lm & lanemask_lt());
+                    if (pos < L.cap) L.slot[pos] = i;
+                    else cls = CLS_WARP;
                 }
             }
             unsigned mm = __ballot_sync(FULL_MASK, cls == CLS_WARP);
@@ -737,7 +774,7 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
                 c = __reduce_add_sync(FULL_MASK, c);
                 if ((int)lane == src) cnt = c;
             }
-            if (CACHE && walked) {  // record the walk (a full neighbourhood just skips it)
+            if (CACHE && (walked || summarised)) {  // record the count (a full neighbourhood just skips it)
                 const unsigned long long w = ((unsigned long long)cnt << 32) | (uint32_t)key;
                 uint32_t sl = j & (CACHE_SLOTS - 1);
                 for (uint32_t t = 0; t < CACHE_PROBES; ++t) {
@@ -761,7 +798,7 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
         if (threadIdx.x == 0) {
             atomicOr(err, DEVERR_TIMEOUT);
             const int other = cur ^ 1;
-            if (BIN_BUFFERS == 2 && s_bin[other] < nbins) {
+            if (BIN_BUFFERS == 2 && s_bin[other] != ~0u) {
                 const uint32_t ph = other ? phase1 : phase0;
                 uint32_t polls = 0;
                 while (!mbar_test_parity(&s_bar[other], ph) && ++polls < COPY_WAIT_LIMIT) {
@@ -791,9 +828,9 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
             per_sm < 1)
             per_sm = 1;
         launch_begin("probe", s);
-        kern<<<num_sms() * per_sm, BIN_PROBE_THREADS, smem, s>>>(qs, g.bin_start, g.nbins, keys, t.offsets, t.H,
+        kern<<<num_sms() * per_sm, BIN_PROBE_THREADS, smem, s>>>(qs, g.bin_start, g.items, keys, t.offsets, t.H,
                                                                  (uint32_t)t.n, counts, total, sink_of(L), work_ctr, t.err,
-                                                                 sorted_limit(t));
+                                                                 sorted_limit(t), t.sum);
         launch_end("probe", s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

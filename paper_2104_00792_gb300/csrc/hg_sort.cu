@@ -3,7 +3,7 @@
 // with their keys).  A query can then count its key in such a bucket with
 // two binary searches (first position >= key, first position > key) instead
 // of walking it, which removes the walk that grows with the number of copies
-// of a key (the duplicate-key regime of Sec. 5.5).  Offsets and each bucket's
+// of a key (the duplicate-key regime of Sec. 5.4).  Offsets and each bucket's
 // multiset are unchanged; only the order inside a bucket, which Algorithm 1
 // leaves free, is fixed.
 //

@@ -74,6 +74,27 @@ def test_zipf_queries_hits_present_misses_absent():
     assert set(wl.keys.tolist()) <= present
 
 
+def test_zipf_weighted_queries_follow_the_key_law():
+    M, q = 1 << 10, 1 << 18
+    wl = W.zipf_weighted(n=1 << 16, num_buckets=1 << 15, q=q, M=M)
+    zt = W.zipf_table(M)
+    H = zt.S[M]
+    vals, counts = np.unique(wl.queries, return_counts=True)
+    freq = dict(zip(vals.tolist(), counts.tolist()))
+    present = {W.rank_value(r) for r in range(1, M + 1)}
+    hits = sum(c for v, c in freq.items() if v in present)
+    assert abs(hits / q - 0.7) < 0.01
+    for r in (1, 2, 3, 8, 32):
+        expect = 0.7 * q / (r * H)
+        got = freq.get(W.rank_value(r), 0)
+        assert abs(got - expect) < 6 * np.sqrt(expect), r
+    # the same keys as zipf_large, and misses never occur among them
+    assert np.array_equal(wl.keys, W.zipf_large(n=1 << 16, num_buckets=1 << 15, q=16, M=M).keys)
+    # hits are drawn from their own stream: the Bernoulli draws match zipf_large's
+    ul = W.zipf_large(n=1 << 16, num_buckets=1 << 15, q=q, M=M).queries
+    assert np.array_equal(np.isin(ul, list(present)), np.isin(wl.queries, list(present)))
+
+
 def test_join_probe_structure():
     wl = W.join_kv(n=1 << 18, num_buckets=1 << 17, q=1 << 14)
     q = wl.queries

@@ -10,18 +10,21 @@ Recipes (master seed ``MASTER_SEED``; stream ids in ``STREAM``):
 * ``plain_uniform`` -- N uniform 32-bit keys (high half of each SplitMix64
   output), Q queries of which a Bernoulli(``hit``) share are copies of a
   uniformly chosen build key and the rest fresh uniform values.  The paper's
-  random-key experiments (Sec. 5.3) draw keys at random; its table size
-  equals the key count (load factor C = 1, Sec. 5.3).
+  random-key experiments (Sec. 4.2) draw keys at random; its table size
+  equals the key count (load factor C = 1, Sec. 4.3).
 * ``zipf_large`` -- N 32-bit keys whose ranks follow Zipf(s=1) over 1..M,
   value = rank * 0x9E3779B1 mod 2^32; queries hit with probability ``hit``
   on a rank drawn uniformly from 1..M, misses use ranks above M (values that
   never occur among the keys).  This is the duplicate-key regime of the
-  paper's Sec. 5.3 "Duplicate Keys" experiment.
+  paper's Sec. 5.4 "Duplicate Keys" experiment.
+* ``zipf_weighted`` -- the same keys, but a hit's rank follows the keys' own
+  Zipf(1) law (stream ``q_rank``), so each value is queried in proportion to
+  its multiplicity: the quadratic regime of the direct walk (Sec. 5.4).
 * ``join_kv`` -- N (uint64 key, uint32 value) pairs, and a probe relation
   whose ``hot_frac`` share of slots holds ``rep`` copies each of hot keys;
   every distinct probe key is a build key with probability 1/2, else fresh;
   slots are Fisher-Yates shuffled.
-* ``duplicate_keys`` -- the duplicate-key experiment (Sec. 5.5): N keys
+* ``duplicate_keys`` -- the duplicate-key experiment (Sec. 5.4): N keys
   uniform over a value range of V = N / 2^d values, so every value occurs
   about 2^d times, with B = V buckets; queries hit (a uniform value of the
   range) with probability ``hit``, else miss (a value above the range).
@@ -53,6 +56,7 @@ STREAM = {
     "q_miss": 4,
     "shuffle": 5,
     "sizes": 6,
+    "q_rank": 7,
 }
 
 _lib = None
@@ -135,6 +139,7 @@ def _load():
         L.hgw_rank_value.restype = ctypes.c_uint32
         L.hgw_rank_value.argtypes = [u64]
         L.hgw_zipf_queries_u32.argtypes = [u64, u64, u64, u64, u64, vp]
+        L.hgw_zipf_weighted_queries_u32.argtypes = [vp, vp, u64, u64, u64, u64, u64, u64, vp]
         L.hgw_join_probe_u64.argtypes = [vp, u64, u64, u64, u64, u64, u64, u64, vp]
         _lib = L
     return _lib
@@ -229,6 +234,15 @@ def zipf_queries(M: int, q: int, hit: float, master: int = MASTER_SEED, salt: in
     return out
 
 
+def zipf_weighted_queries(M: int, q: int, hit: float, master: int = MASTER_SEED, salt: int = 0) -> np.ndarray:
+    zt = zipf_table(M)
+    out = np.empty(q, dtype=np.uint32)
+    _load().hgw_zipf_weighted_queries_u32(_ptr(zt.S), _ptr(zt.G), M, stream("q_select", master, salt),
+                                          stream("q_miss", master, salt), stream("q_rank", master, salt),
+                                          hit_threshold(hit), q, _ptr(out))
+    return out
+
+
 _ZIPF_CACHE: dict[int, ZipfTable] = {}
 
 
@@ -243,6 +257,13 @@ def zipf_large(n: int = 1 << 28, num_buckets: int = 1 << 27, q: int = 1 << 28, M
     keys = zipf_table(M).values(stream("keys", master, salt), n)
     queries = zipf_queries(M, q, hit, master, salt)
     return Workload("zipf_large", keys, None, queries, num_buckets)
+
+
+def zipf_weighted(n: int = 1 << 28, num_buckets: int = 1 << 27, q: int = 1 << 28, M: int = 1 << 24,
+                  hit: float = 0.7, master: int = MASTER_SEED, salt: int = 0) -> Workload:
+    keys = zipf_table(M).values(stream("keys", master, salt), n)
+    queries = zipf_weighted_queries(M, q, hit, master, salt)
+    return Workload("zipf_weighted", keys, None, queries, num_buckets)
 
 
 def join_kv(n: int = 1 << 27, num_buckets: int = 1 << 26, q: int = 1 << 26, hot_frac: float = 0.05,

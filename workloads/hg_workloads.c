@@ -250,6 +250,30 @@ void hgw_zipf_queries_u32(uint64_t M, uint64_t sel, uint64_t miss, uint64_t hit_
     parallel_for(q, zq_body, &c);
 }
 
+/* Zipf-weighted queries: as above, but a hit's rank follows the keys' own
+ * Zipf(1) law, drawn from out(rank, i), so hot values are queried in
+ * proportion to their multiplicity. */
+typedef struct { const double* S; const uint32_t* G; uint64_t M, sel, miss, rank, thr; uint32_t* out; } zwq_ctx;
+
+static void zwq_body(void* p, uint64_t lo, uint64_t hi) {
+    zwq_ctx* c = (zwq_ctx*)p;
+    const uint64_t miss_span = 0xFFFFFFFFULL - c->M;
+    for (uint64_t i = lo; i < hi; ++i) {
+        uint64_t x = sm64_at(c->sel, i);
+        uint64_t r;
+        if ((x >> 32) < c->thr) r = zipf_rank(c->S, c->G, c->M, sm64_at(c->rank, i));
+        else r = c->M + 1 + pick32(sm64_at(c->miss, i) >> 32, miss_span);
+        c->out[i] = rank_value(r);
+    }
+}
+
+void hgw_zipf_weighted_queries_u32(const double* S, const uint32_t* G, uint64_t M, uint64_t sel,
+                                   uint64_t miss, uint64_t rank, uint64_t hit_threshold,
+                                   uint64_t q, uint32_t* out) {
+    zwq_ctx c = {S, G, M, sel, miss, rank, hit_threshold, out};
+    parallel_for(q, zwq_body, &c);
+}
+
 /* ------------------------------------------------------------------ */
 /* Key-value join probe relation with a repeated hot subset.            */
 /*   D distinct probe keys: H hot keys (each placed `rep` times) then    */
