@@ -1,9 +1,12 @@
 """Benchmark: HashGraph build + probe throughput on one GB300 (or N replicas).
 
-One step = hg_build (hash, histogram, scan, scatter) + hg_query_count (counts
-and total) + hg_free over the large duplicate-key workload: 2^28 uint32 keys
-drawn Zipf(s=1) over 2^24 distinct values, 2^27 buckets, murmur3-fmix32 seed
-0, 2^28 queries with 70% hits.  Prints one JSON line.
+One step = hg_build (hash, histogram, scan, scatter; with HG_LONG_SUMMARY the
+long buckets condensed) + hg_query_count (counts and total) + hg_free over the
+large duplicate-key workload: 2^28 uint32 keys drawn Zipf(s=1) over 2^24
+distinct values, 2^27 buckets, murmur3-fmix32 seed 0, 2^28 queries with 70%
+hits (--workload zipf_weighted: hits drawn by the same Zipf law).  The query
+grouping runs on a second stream while the table builds (query plans).
+Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -57,7 +60,7 @@ def parse():
                         "hg_query_count_intersect (HG(Q) + bucket intersections, the paper's query form)")
     p.add_argument("--long-summary", default="auto", choices=["auto", "on", "off"],
                    help="build with HG_LONG_SUMMARY (buckets of more than 8192 keys condensed to their distinct "
-                        "keys); auto = on for zipf_weighted, off for zipf_large")
+                        "keys and counts); auto = on (both workloads' Zipf keys make such buckets)")
     p.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / the plain path's capacity")
     p.add_argument("--budget-gb", type=float, default=100.0, help="serving: device-memory budget for tables")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
@@ -74,9 +77,7 @@ def workload_desc(log2n, weighted=False):
 
 
 def use_summary(args):
-    if args.long_summary == "auto":
-        return args.workload == "zipf_weighted"
-    return args.long_summary == "on"
+    return args.long_summary in ("auto", "on")
 
 
 def cpu_sample_log2(args):

@@ -239,9 +239,10 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const void* d_value
         free_table(t, st);
         return r;
     }
-    e = build_table(*t, d_keys, d_values, st);
+    e = (cfg->flags & HG_LONG_SUMMARY) ? summary_prepare(*t, st) : cudaSuccess;
+    if (e == cudaSuccess) e = build_table(*t, d_keys, d_values, st);
     if (e == cudaSuccess && (cfg->flags & HG_SORTED_BUCKETS)) e = sort_buckets(*t, st);
-    if (e == cudaSuccess && (cfg->flags & HG_LONG_SUMMARY)) e = summarize_long_buckets(*t, st);
+    if (e == cudaSuccess && (cfg->flags & HG_LONG_SUMMARY)) e = summary_finish(*t, st);
     if (e != cudaSuccess) {
         hg_status r = cuda_fail(e, "hg_build");
         free_table(t, st);

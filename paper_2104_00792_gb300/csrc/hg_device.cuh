@@ -151,6 +151,19 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // Slot of bucket b in a long-bucket summary map (linear probing from here).
 __device__ __forceinline__ uint32_t summary_slot(uint32_t b, uint32_t mask) { return fmix32(b ^ 0x2c1b3c6du) & mask; }
 
+// Lists long bucket b: next index l, bucket[l] = b, map entry (l << 32 | b).
+__device__ __forceinline__ void note_long(const LongFinder& F, uint32_t b) {
+    const uint32_t l = atomicAdd(F.n_long, 1u);
+    if (l >= F.cap) return;  // cannot happen: each long bucket holds more than n / (cap + 1) keys
+    F.bucket[l] = b;
+    uint32_t h = summary_slot(b, F.map_mask);
+    const unsigned long long w = ((unsigned long long)l << 32) | b;
+    for (uint32_t probe = 0; probe <= F.map_mask; ++probe) {
+        if (atomicCAS(F.map + h, ~0ull, w) == ~0ull) return;
+        h = (h + 1) & F.map_mask;
+    }
+}
+
 // Count of `key` in long bucket b from its summary (HG_LONG_SUMMARY): false
 // when the bucket has no summary (too many distinct keys, or none was made),
 // so that the caller walks it instead.

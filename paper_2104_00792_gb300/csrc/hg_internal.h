@@ -45,6 +45,15 @@ struct LongSummary {
     const uint32_t* len = nullptr;  // [cap]: entries, or SUM_OVERFLOW
 };
 
+// Where the build lists the buckets of more than SUM_MIN_LEN keys (null map: not wanted).
+struct LongFinder {
+    uint32_t* n_long = nullptr;
+    uint32_t* bucket = nullptr;          // [cap]
+    unsigned long long* map = nullptr;   // bucket -> index, see summary_slot
+    uint32_t map_mask = 0;
+    uint32_t cap = 0;
+};
+
 struct Table {
     uint32_t key_bytes = 4;
     uint32_t has_values = 0;  // values array present (user values or input indices)
@@ -59,6 +68,8 @@ struct Table {
     uint32_t* values = nullptr;   // n or null
     uint32_t* err = nullptr;      // device error word
     LongSummary sum{};            // HG_LONG_SUMMARY
+    LongFinder finder{};          // set before the build when summaries are wanted
+    bool long_noted = false;      // the build listed the long buckets itself
     void* sum_mem = nullptr;
     uint32_t sum_cap = 0;
     const uint32_t* sum_n_long = nullptr;
@@ -88,8 +99,11 @@ cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values
 uint32_t sorted_bucket_max(uint32_t key_bytes);
 cudaError_t sort_buckets(Table& t, cudaStream_t s);
 
-// HG_LONG_SUMMARY: fills t.sum (allocating t.sum_mem); run after the build.
-cudaError_t summarize_long_buckets(Table& t, cudaStream_t s);
+// HG_LONG_SUMMARY: summary_prepare (before the build) allocates t.sum_mem and
+// sets t.finder, through which the partitioned build lists the long buckets;
+// summary_finish (after it) lists them itself if the build did not, and fills t.sum.
+cudaError_t summary_prepare(Table& t, cudaStream_t s);
+cudaError_t summary_finish(Table& t, cudaStream_t s);
 
 // Queries grouped by the table's bins (ranges of 8192 buckets), so that a
 // bin's offsets and keys stay in L1 while its queries are probed; the counts,

@@ -674,7 +674,7 @@ k_huge_count(const K* __restrict__ in, Hasher H, const uint32_t* __restrict__ bi
 __global__ void __launch_bounds__(1024)
 k_huge_scan(const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ huge_bin,
             const Plan* __restrict__ plan, const uint32_t* __restrict__ huge_count, uint32_t* huge_cursor,
-            uint32_t* offsets, uint64_t B) {
+            uint32_t* offsets, uint64_t B, LongFinder LF) {
     __shared__ uint32_t s_warp[33];
     const uint32_t e = blockIdx.x;
     if (e >= plan->n_huge) return;
@@ -689,6 +689,7 @@ k_huge_scan(const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__
         if (j < nb) {
             offsets[b0 + j] = running + ex;
             huge_cursor[(uint64_t)e * BPB + j] = running + ex;
+            if (LF.map && c > SUM_MIN_LEN) note_long(LF, (uint32_t)(b0 + j));
         }
         running += tot;
     }
@@ -704,7 +705,7 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ work,
             const uint32_t* __restrict__ huge_bin, const uint32_t* __restrict__ huge_chunk_start,
             const Plan* __restrict__ plan, uint32_t* huge_cursor, uint32_t* work_ctr, uint32_t* offsets,
-            K* __restrict__ out, uint32_t* __restrict__ out_v, uint32_t* err) {
+            K* __restrict__ out, uint32_t* __restrict__ out_v, uint32_t* err, LongFinder LF) {
     constexpr uint32_t STAGE_CAP = (uint32_t)(LOCAL_STAGE_BYTES / (sizeof(K) + (HV ? 4 : 0)));
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
@@ -816,6 +817,17 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             for (int q = 0; q < NTHR; ++q) {
                 const uint32_t wsum = __reduce_add_sync(FULL_MASK, cold[q]);
                 if (lane == 0) s_red[q][w] = wsum;
+            }
+        }
+        // buckets of more than SUM_MIN_LEN keys (HG_LONG_SUMMARY), only possible in a bin that large
+        if (LF.map && s1 - s0 > SUM_MIN_LEN) {
+#pragma unroll
+            for (int u0 = 0; u0 < CPT; u0 += 4) {
+                const uint4 x = cnt4(u0);
+                const uint32_t cv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (cv[u] > SUM_MIN_LEN) note_long(LF, (uint32_t)(b0 + jt + u0 + u));
             }
         }
         __syncthreads();
@@ -1151,7 +1163,8 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     }
     if (e == cudaSuccess) {
         launch_begin("huge_scan", s);
-        k_huge_scan<<<MAX_HUGE, 1024, 0, s>>>(bin_start, huge_bin, plan, huge_count, huge_cursor, t.offsets, B);
+        k_huge_scan<<<MAX_HUGE, 1024, 0, s>>>(bin_start, huge_bin, plan, huge_count, huge_cursor, t.offsets, B,
+                                              t.finder);
         launch_end("huge_scan", s);
         e = cudaGetLastError();
     }
@@ -1165,7 +1178,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
             launch_begin("bin_build", s);
             kern<<<grid_for(kern, LOCAL_THREADS, smem), LOCAL_THREADS, smem, s>>>(
                 kb, hv ? vb : nullptr, n, t.H, bin_start, work, huge_bin, huge_cs, plan, huge_cursor, ctr,
-                t.offsets, kout, t.values, t.err);
+                t.offsets, kout, t.values, t.err, t.finder);
             launch_end("bin_build", s);
             return cudaGetLastError();
         };
@@ -1334,6 +1347,8 @@ bool partition_supported(uint64_t B) { return (B + BPB - 1) / BPB <= MAX_BINS; }
 
 cudaError_t build_partitioned(Table& t, const void* d_keys, const void* d_values, cudaStream_t s) {
     const uint32_t* vals = static_cast<const uint32_t*>(d_values);
+    // k_bin_local and k_huge_scan list the long buckets when t.finder asks for them
+    t.long_noted = t.finder.map != nullptr;
     if (t.key_bytes == 4) return build_partitioned_impl<uint32_t>(t, static_cast<const uint32_t*>(d_keys), vals, s);
     return build_partitioned_impl<uint64_t>(t, static_cast<const uint64_t*>(d_keys), vals, s);
 }

@@ -11,9 +11,12 @@
 // gets the length SUM_OVERFLOW and is walked as before.
 //
 // Steps, on the build's stream:
-//   k_sum_find    one pass over the offsets (16-byte loads): every long bucket
-//                 takes an index l and enters the bucket -> l hash map;
-//   k_sum_plan    one CTA: SUM_CHUNK-key chunks of each long bucket, prefix sums;
+//   (listing)     every long bucket takes an index l and enters the bucket -> l
+//                 hash map: the partitioned build does it where it writes the
+//                 offsets (k_bin_local, k_huge_scan); after the direct build,
+//                 k_sum_find makes one pass over the offsets (16-byte loads);
+//   k_sum_plan    one CTA: SUM_CHUNK-key chunks of each long bucket, one work
+//                 item descriptor (key range, l) per chunk;
 //   k_sum_count   persistent: one chunk per CTA work item.  Each thread counts
 //                 runs of equal keys in registers and adds each run into a
 //                 shared-memory table; the table is then added into the
@@ -33,20 +36,18 @@ namespace {
 constexpr uint32_t SUM_CHUNK = 1u << 16;  // keys per k_sum_count work item
 constexpr uint32_t SUM_LOCAL = 256;       // slots of a chunk's shared-memory table
 constexpr int SUM_THREADS = 512;
+constexpr int SUM_UNROLL = 4;             // 16-byte loads in flight per thread
 
 // Scratch and result arrays of one table's summaries (one allocation).
 struct SumBuild {
-    uint32_t* n_long;        // [1]
+    LongFinder F;            // n_long [1], bucket [cap], map
     uint32_t* total_chunks;  // [1]
-    uint32_t cap;
-    unsigned long long* map;  // [map_mask + 1]
-    uint32_t map_mask;
-    uint32_t* bucket;       // [cap]
-    uint32_t* chunk_start;  // [cap + 1]
-    uint32_t* spec;         // [cap]: copies of the all-ones key
-    uint32_t* len;          // [cap]: 0 while counting, SUM_OVERFLOW on overflow, then the entry count
-    void* keys;             // [cap * SUM_SLOTS]
-    uint32_t* cnt;          // [cap * SUM_SLOTS]
+    uint4* item;             // [max_items]: (first key, end key, l, 0) of each chunk
+    uint32_t max_items;
+    uint32_t* spec;          // [cap]: copies of the all-ones key
+    uint32_t* len;           // [cap]: 0 while counting, SUM_OVERFLOW on overflow, then the entry count
+    void* keys;              // [cap * SUM_SLOTS]
+    uint32_t* cnt;           // [cap * SUM_SLOTS]
 };
 
 template <typename K>
@@ -61,22 +62,10 @@ __device__ __forceinline__ uint64_t cas_key(uint64_t* p, uint64_t cmp, uint64_t 
                                (unsigned long long)v);
 }
 
-__device__ __forceinline__ void note_long(const SumBuild& S, uint32_t b) {
-    const uint32_t l = atomicAdd(S.n_long, 1u);
-    if (l >= S.cap) return;  // cannot happen: a long bucket holds more than n / cap keys
-    S.bucket[l] = b;
-    uint32_t h = summary_slot(b, S.map_mask);
-    const unsigned long long w = ((unsigned long long)l << 32) | b;
-    for (uint32_t probe = 0; probe <= S.map_mask; ++probe) {
-        if (atomicCAS(S.map + h, ~0ull, w) == ~0ull) return;
-        h = (h + 1) & S.map_mask;
-    }
-}
-
 // Long buckets from the offsets: thread v reads offsets [4v, 4v + 4) with one
 // 16-byte load and takes the fifth from the next lane.
 __global__ void __launch_bounds__(256) k_sum_find(const uint32_t* __restrict__ offs, uint64_t B, uint32_t n_keys,
-                                                  SumBuild S) {
+                                                  LongFinder F) {
     const unsigned lane = lane_id();
     const uint64_t nvec = (B + 3) / 4;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -97,26 +86,27 @@ __global__ void __launch_bounds__(256) k_sum_find(const uint32_t* __restrict__ o
             if (b >= B) break;
             const uint32_t hi = min(e[u + 1], n_keys);
             const uint32_t lo = min(e[u], hi);
-            if (hi - lo > SUM_MIN_LEN) note_long(S, (uint32_t)b);
+            if (hi - lo > SUM_MIN_LEN) note_long(F, (uint32_t)b);
         }
     }
 }
 
-// One CTA: chunk_start[l] = sum over l' < l of ceil(len(l') / SUM_CHUNK).
+// One CTA: the chunks of every long bucket l (chunks before it: the running
+// prefix of ceil(len / SUM_CHUNK)), each written as a work item descriptor.
 __global__ void __launch_bounds__(1024) k_sum_plan(const uint32_t* __restrict__ offs, uint32_t n_keys, SumBuild S) {
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_tot;
     const unsigned lane = lane_id();
     const int w = threadIdx.x >> 5;
-    const uint32_t L = min(*S.n_long, S.cap);
+    const uint32_t L = min(*S.F.n_long, S.F.cap);
     uint32_t running = 0;
     for (uint32_t base = 0; base < L; base += blockDim.x) {
         const uint32_t l = base + threadIdx.x;
-        uint32_t ch = 0;
+        uint32_t ch = 0, lo = 0, hi = 0;
         if (l < L) {
-            const uint32_t b = S.bucket[l];
-            const uint32_t hi = min(offs[b + 1], n_keys);
-            const uint32_t lo = min(offs[b], hi);
+            const uint32_t b = S.F.bucket[l];
+            hi = min(offs[b + 1], n_keys);
+            lo = min(offs[b], hi);
             ch = (hi - lo + SUM_CHUNK - 1) / SUM_CHUNK;
         }
         const uint32_t incl = warp_inclusive_scan(ch);
@@ -129,14 +119,16 @@ __global__ void __launch_bounds__(1024) k_sum_plan(const uint32_t* __restrict__ 
             if (lane == 31) s_tot = wi;
         }
         __syncthreads();
-        if (l < L) S.chunk_start[l] = running + s_warp[w] + incl - ch;
+        const uint32_t first = running + s_warp[w] + incl - ch;
+        for (uint32_t c = 0; c < ch; ++c) {
+            const uint32_t it = first + c;
+            const uint32_t p0 = lo + c * SUM_CHUNK;
+            if (it < S.max_items) S.item[it] = make_uint4(p0, min(hi, p0 + SUM_CHUNK), l, 0u);
+        }
         running += s_tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        S.chunk_start[L] = running;
-        *S.total_chunks = running;
-    }
+    if (threadIdx.x == 0) *S.total_chunks = min(running, S.max_items);
 }
 
 // Chunks of the long buckets: distinct keys and their copies, added into the
@@ -149,23 +141,12 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sum_count(const K* __restrict__
     constexpr K EMPTY = ~(K)0;
     __shared__ K s_key[SUM_LOCAL];
     __shared__ uint32_t s_cnt[SUM_LOCAL];
-    __shared__ uint32_t s_spec, s_over, s_l, s_p0, s_p1;
+    __shared__ uint32_t s_spec, s_over;
     const uint32_t total = *S.total_chunks;
-    const uint32_t L = min(*S.n_long, S.cap);
     for (uint32_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const uint4 d = S.item[item];  // same address in every thread: one broadcast load
+        const uint32_t p0 = min(d.x, n_keys), p1 = min(d.y, n_keys), l = d.z;
         if (threadIdx.x == 0) {
-            uint32_t lo = 0, hi = L;  // last l with chunk_start[l] <= item
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (S.chunk_start[mid] <= item) lo = mid; else hi = mid;
-            }
-            const uint32_t b = S.bucket[lo];
-            const uint32_t e1 = min(offs[b + 1], n_keys);
-            const uint32_t e0 = min(offs[b], e1);
-            const uint32_t p0 = e0 + (item - S.chunk_start[lo]) * SUM_CHUNK;
-            s_l = lo;
-            s_p0 = p0;
-            s_p1 = min(e1, p0 + SUM_CHUNK);
             s_spec = 0;
             s_over = 0;
         }
@@ -174,7 +155,6 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sum_count(const K* __restrict__
             s_cnt[t] = 0;
         }
         __syncthreads();
-        const uint32_t p0 = s_p0, p1 = s_p1;
         // add `c` copies of `k` to the chunk's table
         auto flush = [&](K k, uint32_t c) {
             if (c == 0) return;
@@ -200,31 +180,37 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sum_count(const K* __restrict__
         K r0 = 0, r1 = 0;
         uint32_t c0 = 0, c1 = 0;
         const uint32_t a0 = p0 & ~(uint32_t)(KVEC - 1);
-        for (uint32_t v = a0 + threadIdx.x * KVEC; v < p1; v += blockDim.x * KVEC) {
+        const uint32_t stride = blockDim.x * KVEC;
+        for (uint32_t v = a0 + threadIdx.x * KVEC; v < p1; v += SUM_UNROLL * stride) {
             if (*static_cast<volatile uint32_t*>(&s_over)) break;
-            const KeyVec<K> kv = load_keys16(keys + v);
+            KeyVec<K> kv[SUM_UNROLL];  // SUM_UNROLL loads in flight per thread
 #pragma unroll
-            for (int u = 0; u < KVEC; ++u) {
-                const uint32_t i = v + u;
-                if (i < p0 || i >= p1) continue;
-                const K k = kv.k[u];
-                if (c0 && k == r0) {
-                    ++c0;
-                } else if (c1 && k == r1) {
-                    ++c1;
-                } else {
-                    flush(r1, c1);
-                    r1 = r0;
-                    c1 = c0;
-                    r0 = k;
-                    c0 = 1;
+            for (int r = 0; r < SUM_UNROLL; ++r)
+                if (v + r * stride < p1) kv[r] = load_keys16(keys + v + r * stride);
+#pragma unroll
+            for (int r = 0; r < SUM_UNROLL; ++r) {
+#pragma unroll
+                for (int u = 0; u < KVEC; ++u) {
+                    const uint32_t i = v + r * stride + u;
+                    if (i < p0 || i >= p1) continue;
+                    const K k = kv[r].k[u];
+                    if (c0 && k == r0) {
+                        ++c0;
+                    } else if (c1 && k == r1) {
+                        ++c1;
+                    } else {
+                        flush(r1, c1);
+                        r1 = r0;
+                        c1 = c0;
+                        r0 = k;
+                        c0 = 1;
+                    }
                 }
             }
         }
         flush(r0, c0);
         flush(r1, c1);
         __syncthreads();
-        const uint32_t l = s_l;
         if (s_over) {
             if (threadIdx.x == 0) atomicOr(S.len + l, SUM_OVERFLOW);
         } else {
@@ -258,7 +244,7 @@ __global__ void __launch_bounds__(256) k_sum_finish(SumBuild S) {
     constexpr K EMPTY = ~(K)0;
     constexpr int PER = SUM_SLOTS / 32;
     const unsigned lane = lane_id();
-    const uint32_t L = min(*S.n_long, S.cap);
+    const uint32_t L = min(*S.F.n_long, S.F.cap);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t l = gw; l < L; l += nw) {
@@ -306,64 +292,47 @@ __global__ void __launch_bounds__(256) k_sum_finish(SumBuild S) {
     }
 }
 
-template <typename K>
-cudaError_t summarize_impl(Table& t, cudaStream_t s) {
-    const uint64_t cap64 = t.n / (SUM_MIN_LEN + 1);
-    if (cap64 == 0) return cudaSuccess;
-    const uint32_t cap = (uint32_t)cap64;
-    uint32_t map_slots = 2;
-    while (map_slots < 2 * cap) map_slots <<= 1;
+// Capacity: a long bucket holds more than SUM_MIN_LEN keys, so there are at most n / (SUM_MIN_LEN + 1).
+uint32_t summary_cap(uint64_t n) { return (uint32_t)(n / (SUM_MIN_LEN + 1)); }
+
+SumBuild sum_build_of(const Table& t) {
+    SumBuild S{};
+    S.F = t.finder;
+    char* base = static_cast<char*>(t.sum_mem);
+    const uint32_t cap = t.sum_cap;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    // region set to all ones: map, keys; region set to zero: header, spec, len, counts
     size_t off = 0;
-    const size_t o_map = off; off += al((size_t)map_slots * 8);
-    const size_t o_keys = off; off += al((size_t)cap * SUM_SLOTS * sizeof(K));
-    const size_t ones_end = off;
+    off += al((size_t)(S.F.map_mask + 1) * 8);                  // map
+    const size_t o_keys = off; off += al((size_t)cap * SUM_SLOTS * t.key_bytes);
     const size_t o_hdr = off; off += 256;
     const size_t o_spec = off; off += al((size_t)cap * 4);
     const size_t o_len = off; off += al((size_t)cap * 4);
     const size_t o_cnt = off; off += al((size_t)cap * SUM_SLOTS * 4);
-    const size_t zero_end = off;
-    const size_t o_bucket = off; off += al((size_t)cap * 4);
-    const size_t o_cs = off; off += al(((size_t)cap + 1) * 4);
-    void* mem = nullptr;
-    cudaError_t e = dev_alloc(&mem, off, s);
-    if (e != cudaSuccess) return e;
-    char* base = static_cast<char*>(mem);
-    SumBuild S;
-    S.n_long = reinterpret_cast<uint32_t*>(base + o_hdr);
-    S.total_chunks = S.n_long + 1;
-    S.cap = cap;
-    S.map = reinterpret_cast<unsigned long long*>(base + o_map);
-    S.map_mask = map_slots - 1;
-    S.bucket = reinterpret_cast<uint32_t*>(base + o_bucket);
-    S.chunk_start = reinterpret_cast<uint32_t*>(base + o_cs);
+    off += al((size_t)cap * 4);                                   // bucket
+    const size_t o_item = off;
+    S.total_chunks = reinterpret_cast<uint32_t*>(base + o_hdr) + 1;
+    S.item = reinterpret_cast<uint4*>(base + o_item);
+    S.max_items = (uint32_t)(t.n / SUM_CHUNK + cap);
     S.spec = reinterpret_cast<uint32_t*>(base + o_spec);
     S.len = reinterpret_cast<uint32_t*>(base + o_len);
     S.keys = base + o_keys;
     S.cnt = reinterpret_cast<uint32_t*>(base + o_cnt);
-    t.sum_mem = mem;
-    t.sum_cap = cap;
-    t.sum_n_long = S.n_long;
-    t.sum_bucket = S.bucket;
-    t.sum.map = S.map;
-    t.sum.map_mask = S.map_mask;
-    t.sum.keys = S.keys;
-    t.sum.cnt = S.cnt;
-    t.sum.len = S.len;
+    return S;
+}
 
-    e = cudaMemsetAsync(base, 0xFF, ones_end, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + ones_end, 0, zero_end - ones_end, s);
-    if (e != cudaSuccess) return e;
+template <typename K>
+cudaError_t finish_impl(Table& t, cudaStream_t s) {
+    const SumBuild S = sum_build_of(t);
     const uint32_t n_keys = (uint32_t)t.n;
-    {
+    cudaError_t e;
+    if (!t.long_noted) {
         const uint64_t nvec = (t.B + 3) / 4;
         uint64_t blocks = (nvec + 255) / 256;
         const uint64_t maxb = (uint64_t)num_sms() * 8;
         if (blocks > maxb) blocks = maxb;
         if (blocks < 1) blocks = 1;
         launch_begin("sum_find", s);
-        k_sum_find<<<(unsigned)blocks, 256, 0, s>>>(t.offsets, t.B, n_keys, S);
+        k_sum_find<<<(unsigned)blocks, 256, 0, s>>>(t.offsets, t.B, n_keys, S.F);
         launch_end("sum_find", s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -372,32 +341,70 @@ cudaError_t summarize_impl(Table& t, cudaStream_t s) {
     launch_end("sum_plan", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
-        // at most n / SUM_CHUNK + cap chunks
-        uint64_t items = t.n / SUM_CHUNK + cap;
         uint64_t grid = (uint64_t)num_sms() * 3;
-        if (grid > items) grid = items;
+        if (grid > S.max_items) grid = S.max_items;
         launch_begin("sum_count", s);
         k_sum_count<K><<<(unsigned)grid, SUM_THREADS, 0, s>>>(static_cast<const K*>(t.keys), t.offsets, n_keys, S);
         launch_end("sum_count", s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    {
-        uint64_t blocks = ((uint64_t)cap * 32 + 255) / 256;
-        const uint64_t maxb = (uint64_t)num_sms() * 8;
-        if (blocks > maxb) blocks = maxb;
-        launch_begin("sum_finish", s);
-        k_sum_finish<K><<<(unsigned)blocks, 256, 0, s>>>(S);
-        launch_end("sum_finish", s);
-        e = cudaGetLastError();
-    }
-    return e;
+    uint64_t blocks = ((uint64_t)t.sum_cap * 32 + 255) / 256;
+    const uint64_t maxb = (uint64_t)num_sms() * 8;
+    if (blocks > maxb) blocks = maxb;
+    launch_begin("sum_finish", s);
+    k_sum_finish<K><<<(unsigned)blocks, 256, 0, s>>>(S);
+    launch_end("sum_finish", s);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t summarize_long_buckets(Table& t, cudaStream_t s) {
-    if (t.key_bytes == 4) return summarize_impl<uint32_t>(t, s);
-    return summarize_impl<uint64_t>(t, s);
+cudaError_t summary_prepare(Table& t, cudaStream_t s) {
+    const uint32_t cap = summary_cap(t.n);
+    if (cap == 0) return cudaSuccess;
+    uint32_t map_slots = 2;
+    while (map_slots < 2 * cap) map_slots <<= 1;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    // set to all ones: map, keys; set to zero: header, spec, len, counts; then bucket, items
+    size_t off = 0;
+    const size_t o_map = off; off += al((size_t)map_slots * 8);
+    off += al((size_t)cap * SUM_SLOTS * t.key_bytes);
+    const size_t ones_end = off;
+    const size_t o_hdr = off; off += 256;
+    off += al((size_t)cap * 4);
+    off += al((size_t)cap * 4);
+    off += al((size_t)cap * SUM_SLOTS * 4);
+    const size_t zero_end = off;
+    const size_t o_bucket = off; off += al((size_t)cap * 4);
+    off += al(((size_t)(t.n / SUM_CHUNK) + cap) * 16);
+    void* mem = nullptr;
+    cudaError_t e = dev_alloc(&mem, off, s);
+    if (e != cudaSuccess) return e;
+    char* base = static_cast<char*>(mem);
+    t.sum_mem = mem;
+    t.sum_cap = cap;
+    t.finder.n_long = reinterpret_cast<uint32_t*>(base + o_hdr);
+    t.finder.bucket = reinterpret_cast<uint32_t*>(base + o_bucket);
+    t.finder.map = reinterpret_cast<unsigned long long*>(base + o_map);
+    t.finder.map_mask = map_slots - 1;
+    t.finder.cap = cap;
+    t.sum_n_long = t.finder.n_long;
+    t.sum_bucket = t.finder.bucket;
+    const SumBuild S = sum_build_of(t);
+    t.sum.map = t.finder.map;
+    t.sum.map_mask = t.finder.map_mask;
+    t.sum.keys = S.keys;
+    t.sum.cnt = S.cnt;
+    t.sum.len = S.len;
+    e = cudaMemsetAsync(base, 0xFF, ones_end, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + ones_end, 0, zero_end - ones_end, s);
+    return e;
+}
+
+cudaError_t summary_finish(Table& t, cudaStream_t s) {
+    if (!t.sum_mem) return cudaSuccess;
+    if (t.key_bytes == 4) return finish_impl<uint32_t>(t, s);
+    return finish_impl<uint64_t>(t, s);
 }
 
 }  // namespace hg
