@@ -608,7 +608,8 @@ template <typename K, int OUT, bool TOTAL>
 __global__ void __launch_bounds__(BIN_PROBE_THREADS, BIN_PROBE_CTAS_PER_SM)
 k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, BinWork W,
              const K* __restrict__ keys, const uint32_t* __restrict__ offs, Hasher H, uint32_t n_keys, void* counts,
-             uint64_t* total, LongSink L, uint32_t* work_ctr, uint32_t* err, uint32_t sorted_max, LongSummary S) {
+             uint64_t* total, LongSink L, uint32_t* work_ctr, uint32_t* err, uint32_t sorted_max, LongSummary S,
+             const uint32_t* __restrict__ list, const uint32_t* __restrict__ n_list) {
     constexpr uint32_t KVEC = 16 / sizeof(K);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -631,8 +632,16 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
     __syncthreads();
     // thread 0: claim the next work item (a slice of a huge bin's queries, or a
     // whole bin) and start the copies of its bin into buffer b
+    // (with a list: only the listed items)
     auto issue = [&](int b) {
-        const uint32_t item = atomicAdd(work_ctr, 1u);
+        uint32_t item = atomicAdd(work_ctr, 1u);
+        if (list) {
+            if (item >= *n_list) {
+                s_bin[b] = ~0u;
+                return;
+            }
+            item = list[item];
+        }
         if (item >= n_items) {
             s_bin[b] = ~0u;
             return;
@@ -813,11 +822,226 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
     }
 }
 
+// Grouped probe by hash join (32-bit keys): the paper's per-bucket list
+// intersection done a bin at a time through a table of the bin's distinct keys.
+// A CTA takes one bin (a work item covering all its queries), brings the bin's
+// keys into shared memory by a bulk copy, counts them into a shared-memory
+// open-addressing table of (count << 32 | key) words (zero = empty: a present
+// key has a count of at least one) -- each warp reads 32 consecutive keys, and
+// only the first lane of each run of equal keys inserts, with the run's length
+// -- and answers every query with one table lookup (one 8-byte word): the
+// count of a key in its bin is its count in its bucket.  Items this kernel does
+// not take go to a list for k_probe_bins: slices of bins with very many queries,
+// bins whose keys do not fit, and bins with more distinct keys than the table
+// holds (if most bins are like that, the rest are not tried).
+constexpr uint32_t HJ_SLOTS = 2048;                   // table words (16 KiB)
+constexpr uint32_t HJ_MAX_FILL = HJ_SLOTS * 3 / 4;    // distinct keys before the bin falls back
+constexpr uint32_t HJ_KEY_BYTES = 96 * 1024;          // staged keys
+constexpr int HJ_THREADS = 512;
+constexpr uint32_t HJ_TRY_LIMIT = 64;                 // fallbacks before the try-rate test applies
+constexpr int HJ_QUNROLL = 8;                         // query loads in flight per thread
+
+__device__ __forceinline__ uint32_t hj_slot(uint32_t k) {
+    uint32_t x = k * 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    return x >> (32 - 11);  // HJ_SLOTS = 2^11
+}
+static_assert(HJ_SLOTS == 2048, "hj_slot returns 11 bits");
+
+template <int OUT, bool TOTAL>
+__global__ void __launch_bounds__(HJ_THREADS, 2)
+k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_start, BinWork W,
+             const uint32_t* __restrict__ keys, const uint32_t* __restrict__ offs, uint64_t B, uint32_t n_keys,
+             void* counts, uint64_t* total, uint32_t* work_ctr, uint32_t* fb_list, uint32_t* fb_n, uint32_t* tries,
+             uint32_t* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long* s_ht = reinterpret_cast<unsigned long long*>(smem);
+    const uint32_t* s_keys = reinterpret_cast<const uint32_t*>(smem + HJ_SLOTS * 8);
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_p, s_k0, s_k1, s_klo, s_q0, s_q1, s_fill, s_abort;
+    const unsigned lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t huge_items = *W.huge_chunks;
+    const uint32_t n_items = huge_items + *W.n_work;
+    uint64_t acc = 0;
+    uint32_t phase = 0;
+    bool failed = false;
+    // thread 0: claim items until one is taken here (the others go to the
+    // fallback list) and start the copy of its keys; s_p = ~0u when none is left
+    auto claim = [&]() {
+        s_p = ~0u;
+        while (true) {
+            const uint32_t item = atomicAdd(work_ctr, 1u);
+            if (item >= n_items) return;
+            bool fb = item < huge_items;
+            uint32_t p = 0, k0 = 0, k1 = 0, q0 = 0, q1 = 0;
+            if (!fb) {
+                p = W.work[item - huge_items];
+                q0 = qbin_start[p];
+                q1 = qbin_start[p + 1];
+                if (q0 == q1) continue;  // no queries in this bin
+                const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
+                const uint64_t b1 = min(B, b0 + BIN_BUCKETS);
+                k0 = min(__ldg(offs + b0), n_keys);
+                k1 = max(k0, min(__ldg(offs + b1), n_keys));
+                const volatile uint32_t* vt = tries;
+                const bool give_up = vt[1] >= HJ_TRY_LIMIT && 2 * vt[1] >= vt[0];
+                fb = give_up || (uint64_t)(k1 - (k0 & ~3u)) * 4 > HJ_KEY_BYTES;
+            }
+            if (fb) {
+                fb_list[atomicAdd(fb_n, 1u)] = item;
+                continue;
+            }
+            atomicAdd(tries, 1u);
+            const uint32_t klo = k0 & ~3u;
+            const uint32_t bytes = ((k1 - klo) * 4 + 15) & ~15u;
+            s_p = item;
+            s_k0 = k0;
+            s_k1 = k1;
+            s_klo = klo;
+            s_q0 = q0;
+            s_q1 = q1;
+            fence_proxy_async_smem();  // the key buffer's earlier reads come before the copy's writes
+            mbar_arrive_expect_tx(&s_bar, bytes);
+            if (bytes) bulk_load(smem + HJ_SLOTS * 8, keys + klo, bytes, &s_bar);
+            return;
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        claim();
+        s_fill = 0;
+        s_abort = 0;
+    }
+    for (uint32_t t = threadIdx.x; t < HJ_SLOTS; t += blockDim.x) s_ht[t] = 0ull;
+    __syncthreads();
+    while (true) {
+        // here: the table is empty, and the copy of item s_p's keys is in flight
+        const uint32_t item = s_p;
+        if (item == ~0u) break;
+        {
+            uint32_t polls = 0;
+            while (!mbar_test_parity(&s_bar, phase) && ++polls < COPY_WAIT_LIMIT) {
+            }
+            failed = polls >= COPY_WAIT_LIMIT;
+            phase ^= 1;
+        }
+        if (__syncthreads_or(failed)) break;
+        const uint32_t k0 = s_k0, k1 = s_k1, kofs = s_k0 - s_klo;
+        const uint32_t q0 = s_q0, q1 = s_q1;
+        // count the bin's keys: runs of equal keys inside each 32-key step, one insert per run
+        for (uint32_t base = warp * 32; base < k1 - k0; base += nwarps * 32) {
+            if (*static_cast<volatile uint32_t*>(&s_abort)) break;
+            const uint32_t nv = min(32u, (k1 - k0) - base);
+            const bool valid = lane < nv;
+            const uint32_t k = valid ? s_keys[kofs + base + lane] : 0u;
+            const uint32_t prev = __shfl_up_sync(FULL_MASK, k, 1);
+            const bool head = valid && (lane == 0 || k != prev);
+            const unsigned hm = __ballot_sync(FULL_MASK, head);
+            if (head) {
+                const unsigned above = lane == 31 ? 0u : (hm & ~((2u << lane) - 1u));
+                const uint32_t len = (above ? (uint32_t)(__ffs(above) - 1) : nv) - lane;
+                const unsigned long long add = (unsigned long long)len << 32;
+                uint32_t sl = hj_slot(k);
+                for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
+                    unsigned long long w = *static_cast<volatile unsigned long long*>(&s_ht[sl]);
+                    if (w == 0ull) {
+                        w = atomicCAS(&s_ht[sl], 0ull, add | k);
+                        if (w == 0ull) {
+                            if (atomicAdd(&s_fill, 1u) + 1 > HJ_MAX_FILL) s_abort = 1;
+                            break;
+                        }
+                    }
+                    if ((uint32_t)w == k) {
+                        atomicAdd(&s_ht[sl], add);
+                        break;
+                    }
+                    sl = (sl + 1) & (HJ_SLOTS - 1);
+                }
+            }
+        }
+        __syncthreads();
+        const bool abort = s_abort != 0;
+        __syncthreads();  // every thread has read this item's shared state
+        if (threadIdx.x == 0) {
+            if (abort) {
+                fb_list[atomicAdd(fb_n, 1u)] = item;
+                atomicAdd(tries + 1, 1u);
+            }
+            // the keys are counted: the next item's copy overlaps this item's queries
+            claim();
+            s_fill = 0;
+            s_abort = 0;
+        }
+        if (!abort) {
+            // answer the bin's queries: one lookup each, HJ_QUNROLL query loads in flight per thread
+            for (uint32_t g0 = q0; g0 < q1; g0 += blockDim.x * HJ_QUNROLL) {
+                uint32_t kq[HJ_QUNROLL];
+#pragma unroll
+                for (int u = 0; u < HJ_QUNROLL; ++u) {
+                    const uint32_t i = g0 + u * blockDim.x + threadIdx.x;
+                    kq[u] = i < q1 ? __ldg(qs + i) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < HJ_QUNROLL; ++u) {
+                    const uint32_t i = g0 + u * blockDim.x + threadIdx.x;
+                    if (i < q1) {
+                        uint32_t sl = hj_slot(kq[u]), cnt = 0;
+                        for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
+                            const unsigned long long w = s_ht[sl];
+                            if (w == 0ull) break;
+                            if ((uint32_t)w == kq[u]) {
+                                cnt = (uint32_t)(w >> 32);
+                                break;
+                            }
+                            sl = (sl + 1) & (HJ_SLOTS - 1);
+                        }
+                        if (OUT == OUT_U32) static_cast<uint32_t*>(counts)[i] = cnt;
+                        acc += cnt;
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the table's last reader is done
+        for (uint32_t t = threadIdx.x; t < HJ_SLOTS; t += blockDim.x) s_ht[t] = 0ull;
+        __syncthreads();
+    }
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(err, DEVERR_TIMEOUT);
+        return;
+    }
+    if (TOTAL) {
+        const uint64_t sum = block_sum(acc);
+        if (threadIdx.x == 0 && sum) atomicAdd(reinterpret_cast<unsigned long long*>(total), (unsigned long long)sum);
+    }
+}
+
 template <typename K, int OUT, bool TOTAL>
 cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts, uint64_t* total,
-                           const LongList& L, uint32_t* work_ctr, cudaStream_t s) {
+                           const LongList& L, uint32_t* ctrs, uint32_t* fb_list, cudaStream_t s) {
     const K* keys = static_cast<const K*>(t.keys);
     const K* qs = static_cast<const K*>(g.q_grouped);
+    // ctrs (zeroed): [0] hash-join work counter, [1] k_probe_bins work counter,
+    // [2] fallback list length, [3..4] bins tried / given up by the hash join
+    const uint32_t* list = nullptr;
+    if constexpr (sizeof(K) == 4) {
+        auto kern = k_probe_hash<OUT, TOTAL>;
+        const size_t smem = (size_t)HJ_SLOTS * 8 + HJ_KEY_BYTES;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, HJ_THREADS, smem) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        launch_begin("probe_hash", s);
+        kern<<<num_sms() * per_sm, HJ_THREADS, smem, s>>>(qs, g.bin_start, g.items, keys, t.offsets, t.B, (uint32_t)t.n,
+                                                          counts, total, ctrs, fb_list, ctrs + 2, ctrs + 3, t.err);
+        launch_end("probe_hash", s);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        list = fb_list;
+    }
     {
         auto kern = k_probe_bins<K, OUT, TOTAL>;
         const size_t smem = BIN_BUFFERS * (size_t)BIN_BUF_BYTES;
@@ -829,8 +1053,8 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
             per_sm = 1;
         launch_begin("probe", s);
         kern<<<num_sms() * per_sm, BIN_PROBE_THREADS, smem, s>>>(qs, g.bin_start, g.items, keys, t.offsets, t.H,
-                                                                 (uint32_t)t.n, counts, total, sink_of(L), work_ctr, t.err,
-                                                                 sorted_limit(t), t.sum);
+                                                                 (uint32_t)t.n, counts, total, sink_of(L), ctrs + 1, t.err,
+                                                                 sorted_limit(t), t.sum, list, list ? ctrs + 2 : nullptr);
         launch_end("probe", s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -858,15 +1082,18 @@ cudaError_t count_grouped(const Table& t, const GroupedQueries& g, uint64_t q, u
     if (e != cudaSuccess) return e;
     void* cmem = nullptr;
     const size_t cbytes = ((q + 4) * 4 + 255) & ~size_t(255);
-    e = dev_alloc(&cmem, 256 + (counts ? 2 * cbytes : 0), s);
+    // the hash join's fallback list: at most one entry per work item
+    const size_t fb_bytes = ((size_t)g.nbins + q / g.items.huge_chunk + 1024) * 4;
+    e = dev_alloc(&cmem, 256 + fb_bytes + (counts ? 2 * cbytes : 0), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(cmem, 0, 256, s);
     if (e == cudaSuccess) {
-        uint32_t* work_ctr = static_cast<uint32_t*>(cmem);
-        uint32_t* cs = counts ? reinterpret_cast<uint32_t*>(static_cast<char*>(cmem) + 256) : nullptr;
+        uint32_t* ctrs = static_cast<uint32_t*>(cmem);
+        uint32_t* fb_list = reinterpret_cast<uint32_t*>(static_cast<char*>(cmem) + 256);
+        uint32_t* cs = counts ? reinterpret_cast<uint32_t*>(static_cast<char*>(cmem) + 256 + fb_bytes) : nullptr;
         uint32_t* tmp = counts ? cs + cbytes / 4 : nullptr;
-        if (counts && total) e = run_probe_bins<K, OUT_U32, true>(t, g, cs, total, L, work_ctr, s);
-        else if (counts) e = run_probe_bins<K, OUT_U32, false>(t, g, cs, nullptr, L, work_ctr, s);
-        else e = run_probe_bins<K, OUT_NONE, true>(t, g, nullptr, total, L, work_ctr, s);
+        if (counts && total) e = run_probe_bins<K, OUT_U32, true>(t, g, cs, total, L, ctrs, fb_list, s);
+        else if (counts) e = run_probe_bins<K, OUT_U32, false>(t, g, cs, nullptr, L, ctrs, fb_list, s);
+        else e = run_probe_bins<K, OUT_NONE, true>(t, g, nullptr, total, L, ctrs, fb_list, s);
         if (e == cudaSuccess && counts) e = ungroup_counts(t, &g, cs, tmp, counts, s);
     }
     if (cmem) dev_free(cmem, s);

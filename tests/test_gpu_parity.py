@@ -293,6 +293,28 @@ def test_grouped_probe_zipf_u32_two_passes(hg):
     _probe_only(hg, wl.keys, 1 << 23, wl.queries)
 
 
+def test_grouped_hash_join_bins(hg):
+    # 1024 bins of ~8192 Zipf keys (at most a few hundred distinct each): the
+    # grouped probe counts each bin through a shared-memory table of its
+    # distinct keys.  Bins 3, 7 and 500 get ~3000 extra distinct keys, more
+    # than the table takes, and fall back to the walking probe; the keys 0 and
+    # 2^32 - 1 (the table's empty marker) occur many times.
+    B = 1 << 23
+    wl = W.zipf_large(n=(1 << 23) + 11, num_buckets=B, q=(1 << 21) + 3, M=1 << 18, salt=13)
+    keys = wl.keys.copy()
+    keys[::97] = 0xFFFFFFFF
+    keys[5::101] = 0
+    rng = np.random.default_rng(14)
+    extra = rng.integers(0, 1 << 32, size=1 << 22, dtype=np.uint64).astype(np.uint32)
+    extra = extra[np.isin(oracle.buckets(extra, B, 0) >> 13, [3, 7, 500])][:9000]
+    keys = np.concatenate([keys, extra])
+    queries = wl.queries.copy()
+    queries[::50] = 0xFFFFFFFF
+    queries[7::51] = 0
+    queries[: extra.size] = extra
+    _probe_only(hg, keys, B, queries)
+
+
 def test_large_table_few_bins(hg):
     # 2^20 buckets = 128 bins, fewer than the probe's CTAs: the direct probe answers
     # a table larger than L2 (grouping needs several bins per SM)
