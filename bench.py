@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--log2n", type=int, default=28, help="log2 of build keys (queries equal, buckets half)")
+    p.add_argument("--zipf-log2m", type=int, default=24, help="log2 of the Zipf workloads' distinct values")
     p.add_argument("--cpu-sample-log2", type=int, default=27)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -68,12 +69,12 @@ def parse():
     return p.parse_args()
 
 
-def workload_desc(log2n, weighted=False):
+def workload_desc(log2n, weighted=False, log2m=24):
     if weighted:
-        return (f"zipf_weighted: N=2^{log2n} uint32 keys Zipf(s=1) over 2^24 values, B=2^{log2n - 1} buckets, "
+        return (f"zipf_weighted: N=2^{log2n} uint32 keys Zipf(s=1) over 2^{log2m} values, B=2^{log2n - 1} buckets, "
                 f"murmur3-fmix32 seed 0, Q=2^{log2n} queries 70% hits (ranks Zipf(s=1) like the keys)")
-    return (f"zipf_large: N=2^{log2n} uint32 keys Zipf(s=1) over 2^24 values, B=2^{log2n - 1} buckets, "
-            f"murmur3-fmix32 seed 0, Q=2^{log2n} queries 70% hits (ranks uniform over the 2^24 values)")
+    return (f"zipf_large: N=2^{log2n} uint32 keys Zipf(s=1) over 2^{log2m} values, B=2^{log2n - 1} buckets, "
+            f"murmur3-fmix32 seed 0, Q=2^{log2n} queries 70% hits (ranks uniform over the 2^{log2m} values)")
 
 
 def use_summary(args):
@@ -104,10 +105,10 @@ def aggregate_gkeys(world, keys_per_rank, ms):
     return world * keys_per_rank / (ms * 1e-3) / 1e9
 
 
-def make_workload(log2n, salt, weighted=False):
+def make_workload(log2n, salt, weighted=False, log2m=24):
     import workloads as W
     make = W.zipf_weighted if weighted else W.zipf_large
-    return make(n=1 << log2n, num_buckets=1 << (log2n - 1), q=1 << log2n, M=1 << 24, hit=0.7, salt=salt)
+    return make(n=1 << log2n, num_buckets=1 << (log2n - 1), q=1 << log2n, M=1 << log2m, hit=0.7, salt=salt)
 
 
 class ClockSampler:
@@ -247,7 +248,7 @@ def cpu_oracle_sample(wl, log2s):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = make_workload(args.log2n, 0, args.workload == "zipf_weighted")
+    wl = make_workload(args.log2n, 0, args.workload == "zipf_weighted", args.zipf_log2m)
     times = []
     res = None
     for _ in range(args.warmup):
@@ -260,7 +261,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": workload_desc(args.log2n, args.workload == "zipf_weighted"),
+            "config": {"workload": workload_desc(args.log2n, args.workload == "zipf_weighted", args.zipf_log2m),
                        "reference": "CPU oracle (oracle/hg_oracle.c)"},
             "cpu_baseline": res, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
@@ -348,7 +349,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     weighted = args.workload == "zipf_weighted"
-    wl = make_workload(args.log2n, rank, weighted)
+    wl = make_workload(args.log2n, rank, weighted, args.zipf_log2m)
     flags = hg.HG_LONG_SUMMARY if use_summary(args) else 0
     N, Q, B = wl.keys.size, wl.queries.size, wl.num_buckets
     keys = torch.from_numpy(wl.keys.view(np.int32)).to(dev)
@@ -497,7 +498,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": workload_desc(args.log2n, weighted), "parallelism": f"replicas{world}",
+        "config": {"workload": workload_desc(args.log2n, weighted, args.zipf_log2m), "parallelism": f"replicas{world}",
                    "build_flags": "HG_LONG_SUMMARY" if flags else "none",
                    "l2": "inputs exceed L2 (2 GiB read per step); no flush",
                    "step": {"plan": "hg_build, with hg_query_plan_create on a second stream, then "

@@ -931,36 +931,56 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
         if (__syncthreads_or(failed)) break;
         const uint32_t k0 = s_k0, k1 = s_k1, kofs = s_k0 - s_klo;
         const uint32_t q0 = s_q0, q1 = s_q1;
-        // count the bin's keys: runs of equal keys inside each 32-key step, one insert per run
-        for (uint32_t base = warp * 32; base < k1 - k0; base += nwarps * 32) {
-            if (*static_cast<volatile uint32_t*>(&s_abort)) break;
-            const uint32_t nv = min(32u, (k1 - k0) - base);
-            const bool valid = lane < nv;
-            const uint32_t k = valid ? s_keys[kofs + base + lane] : 0u;
-            const uint32_t prev = __shfl_up_sync(FULL_MASK, k, 1);
-            const bool head = valid && (lane == 0 || k != prev);
-            const unsigned hm = __ballot_sync(FULL_MASK, head);
-            if (head) {
-                const unsigned above = lane == 31 ? 0u : (hm & ~((2u << lane) - 1u));
-                const uint32_t len = (above ? (uint32_t)(__ffs(above) - 1) : nv) - lane;
-                const unsigned long long add = (unsigned long long)len << 32;
-                uint32_t sl = hj_slot(k);
-                for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
-                    unsigned long long w = *static_cast<volatile unsigned long long*>(&s_ht[sl]);
+        // the bin's first queries are loaded now: their latency overlaps the table's build
+        uint32_t kq[HJ_QUNROLL];
+#pragma unroll
+        for (int u = 0; u < HJ_QUNROLL; ++u) {
+            const uint32_t i = q0 + u * blockDim.x + threadIdx.x;
+            kq[u] = i < q1 ? __ldg(qs + i) : 0u;
+        }
+        // count the bin's keys: runs of equal keys inside each 32-key step, one
+        // insert per run; two steps per iteration for independent loads
+        auto insert = [&](uint32_t k, uint32_t len) {
+            const unsigned long long add = (unsigned long long)len << 32;
+            uint32_t sl = hj_slot(k);
+            for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
+                unsigned long long w = *static_cast<volatile unsigned long long*>(&s_ht[sl]);
+                if (w == 0ull) {
+                    w = atomicCAS(&s_ht[sl], 0ull, add | k);
                     if (w == 0ull) {
-                        w = atomicCAS(&s_ht[sl], 0ull, add | k);
-                        if (w == 0ull) {
-                            if (atomicAdd(&s_fill, 1u) + 1 > HJ_MAX_FILL) s_abort = 1;
-                            break;
-                        }
+                        if (atomicAdd(&s_fill, 1u) + 1 > HJ_MAX_FILL) s_abort = 1;
+                        return;
                     }
-                    if ((uint32_t)w == k) {
-                        atomicAdd(&s_ht[sl], add);
-                        break;
-                    }
-                    sl = (sl + 1) & (HJ_SLOTS - 1);
                 }
+                if ((uint32_t)w == k) {
+                    atomicAdd(&s_ht[sl], add);
+                    return;
+                }
+                sl = (sl + 1) & (HJ_SLOTS - 1);
             }
+        };
+        // run heads of a 32-key step: (key, run length) for the lanes that start a run
+        auto runs = [&](uint32_t nv, uint32_t k, uint32_t& len) {
+            const uint32_t prev = __shfl_up_sync(FULL_MASK, k, 1);
+            const bool head = lane < nv && (lane == 0 || k != prev);
+            const unsigned hm = __ballot_sync(FULL_MASK, head);
+            const unsigned above = lane == 31 ? 0u : (hm & ~((2u << lane) - 1u));
+            len = (above ? (uint32_t)(__ffs(above) - 1) : nv) - lane;
+            return head;
+        };
+        const uint32_t nk = k1 - k0;
+        for (uint32_t base = warp * 32; base < nk; base += 2 * nwarps * 32) {
+            if (*static_cast<volatile uint32_t*>(&s_abort)) break;
+            const uint32_t base2 = base + nwarps * 32;
+            const uint32_t nv1 = min(32u, nk - base);
+            const uint32_t nv2 = base2 < nk ? min(32u, nk - base2) : 0u;
+            const uint32_t ka = lane < nv1 ? s_keys[kofs + base + lane] : 0u;
+            const uint32_t kb = lane < nv2 ? s_keys[kofs + base2 + lane] : 0u;
+            uint32_t la, lb;
+            const bool ha = runs(nv1, ka, la);
+            const bool hb = runs(nv2, kb, lb);
+            if (ha) insert(ka, la);
+            if (hb) insert(kb, lb);
         }
         __syncthreads();
         const bool abort = s_abort != 0;
@@ -976,13 +996,14 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
             s_abort = 0;
         }
         if (!abort) {
-            // answer the bin's queries: one lookup each, HJ_QUNROLL query loads in flight per thread
+            // answer the bin's queries: one lookup each; the next HJ_QUNROLL query
+            // loads per thread are in flight while the current ones are answered
             for (uint32_t g0 = q0; g0 < q1; g0 += blockDim.x * HJ_QUNROLL) {
-                uint32_t kq[HJ_QUNROLL];
+                uint32_t kn[HJ_QUNROLL];
 #pragma unroll
                 for (int u = 0; u < HJ_QUNROLL; ++u) {
-                    const uint32_t i = g0 + u * blockDim.x + threadIdx.x;
-                    kq[u] = i < q1 ? __ldg(qs + i) : 0u;
+                    const uint32_t i = g0 + (HJ_QUNROLL + u) * blockDim.x + threadIdx.x;
+                    kn[u] = i < q1 ? __ldg(qs + i) : 0u;
                 }
 #pragma unroll
                 for (int u = 0; u < HJ_QUNROLL; ++u) {
@@ -1002,6 +1023,8 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
                         acc += cnt;
                     }
                 }
+#pragma unroll
+                for (int u = 0; u < HJ_QUNROLL; ++u) kq[u] = kn[u];
             }
         }
         __syncthreads();  // the table's last reader is done
