@@ -827,27 +827,31 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
 // A CTA takes one bin (a work item covering all its queries), brings the bin's
 // keys into shared memory by a bulk copy, counts them into a shared-memory
 // open-addressing table of (count << 32 | key) words (zero = empty: a present
-// key has a count of at least one) -- each warp reads 32 consecutive keys, and
-// only the first lane of each run of equal keys inserts, with the run's length
-// -- and answers every query with one table lookup (one 8-byte word): the
+// key has a count of at least one; double hashing, so probe sequences do not
+// cluster and a warp's 32 lookups end together) -- each warp reads 32
+// consecutive keys, and only the first lane of each run of equal keys inserts,
+// with the run's length -- and answers every query with one table lookup: the
 // count of a key in its bin is its count in its bucket.  Items this kernel does
 // not take go to a list for k_probe_bins: slices of bins with very many queries,
 // bins whose keys do not fit, and bins with more distinct keys than the table
 // holds (if most bins are like that, the rest are not tried).
-constexpr uint32_t HJ_SLOTS = 2048;                   // table words (16 KiB)
+constexpr uint32_t HJ_SLOTS = 4096;                   // table words (32 KiB)
 constexpr uint32_t HJ_MAX_FILL = HJ_SLOTS * 3 / 4;    // distinct keys before the bin falls back
-constexpr uint32_t HJ_KEY_BYTES = 96 * 1024;          // staged keys
+constexpr uint32_t HJ_KEY_BYTES = 80 * 1024;          // staged keys (two CTAs per SM)
 constexpr int HJ_THREADS = 512;
 constexpr uint32_t HJ_TRY_LIMIT = 64;                 // fallbacks before the try-rate test applies
 constexpr int HJ_QUNROLL = 8;                         // query loads in flight per thread
 
-__device__ __forceinline__ uint32_t hj_slot(uint32_t k) {
+// first slot (top 12 bits of a mix of the key) and probe step (odd, so the
+// sequence visits every slot of the power-of-two table)
+__device__ __forceinline__ void hj_probe_seq(uint32_t k, uint32_t& slot, uint32_t& step) {
     uint32_t x = k * 0x7feb352du;
     x ^= x >> 15;
     x *= 0x846ca68bu;
-    return x >> (32 - 11);  // HJ_SLOTS = 2^11
+    slot = x >> (32 - 12);
+    step = (x >> 7) | 1u;
 }
-static_assert(HJ_SLOTS == 2048, "hj_slot returns 11 bits");
+static_assert(HJ_SLOTS == 4096, "hj_probe_seq returns 12-bit slots");
 
 template <int OUT, bool TOTAL>
 __global__ void __launch_bounds__(HJ_THREADS, 2)
@@ -942,7 +946,8 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
         // insert per run; two steps per iteration for independent loads
         auto insert = [&](uint32_t k, uint32_t len) {
             const unsigned long long add = (unsigned long long)len << 32;
-            uint32_t sl = hj_slot(k);
+            uint32_t sl, stp;
+            hj_probe_seq(k, sl, stp);
             for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
                 unsigned long long w = *static_cast<volatile unsigned long long*>(&s_ht[sl]);
                 if (w == 0ull) {
@@ -956,7 +961,7 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
                     atomicAdd(&s_ht[sl], add);
                     return;
                 }
-                sl = (sl + 1) & (HJ_SLOTS - 1);
+                sl = (sl + stp) & (HJ_SLOTS - 1);
             }
         };
         // run heads of a 32-key step: (key, run length) for the lanes that start a run
@@ -1009,7 +1014,8 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
                 for (int u = 0; u < HJ_QUNROLL; ++u) {
                     const uint32_t i = g0 + u * blockDim.x + threadIdx.x;
                     if (i < q1) {
-                        uint32_t sl = hj_slot(kq[u]), cnt = 0;
+                        uint32_t sl, stp, cnt = 0;
+                        hj_probe_seq(kq[u], sl, stp);
                         for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
                             const unsigned long long w = s_ht[sl];
                             if (w == 0ull) break;
@@ -1017,7 +1023,7 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
                                 cnt = (uint32_t)(w >> 32);
                                 break;
                             }
-                            sl = (sl + 1) & (HJ_SLOTS - 1);
+                            sl = (sl + stp) & (HJ_SLOTS - 1);
                         }
                         if (OUT == OUT_U32) static_cast<uint32_t*>(counts)[i] = cnt;
                         acc += cnt;

@@ -296,7 +296,7 @@ def test_grouped_probe_zipf_u32_two_passes(hg):
 def test_grouped_hash_join_bins(hg):
     # 1024 bins of ~8192 Zipf keys (at most a few hundred distinct each): the
     # grouped probe counts each bin through a shared-memory table of its
-    # distinct keys.  Bins 3, 7 and 500 get ~3000 extra distinct keys, more
+    # distinct keys.  Bins 3, 7 and 500 get ~4000 extra distinct keys, more
     # than the table takes, and fall back to the walking probe; the keys 0 and
     # 2^32 - 1 (the table's empty marker) occur many times.
     B = 1 << 23
@@ -306,7 +306,7 @@ def test_grouped_hash_join_bins(hg):
     keys[5::101] = 0
     rng = np.random.default_rng(14)
     extra = rng.integers(0, 1 << 32, size=1 << 22, dtype=np.uint64).astype(np.uint32)
-    extra = extra[np.isin(oracle.buckets(extra, B, 0) >> 13, [3, 7, 500])][:9000]
+    extra = extra[np.isin(oracle.buckets(extra, B, 0) >> 13, [3, 7, 500])][:12000]
     keys = np.concatenate([keys, extra])
     queries = wl.queries.copy()
     queries[::50] = 0xFFFFFFFF
