@@ -54,6 +54,18 @@ __device__ __forceinline__ uint4 ld_stream16(const void* p) {
     return v;
 }
 
+// Streaming 16-byte load that asks L2 to keep the line (evict_last): for data
+// the same kernel reads again shortly.
+__device__ __forceinline__ uint4 ld_keep16(const void* p) {
+    uint4 v;
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
 template <typename K>
 struct KeyVec {
     static constexpr int N = 16 / sizeof(K);

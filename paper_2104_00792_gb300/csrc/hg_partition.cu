@@ -90,7 +90,8 @@ __device__ __forceinline__ uint32_t bin_of(K k, const Hasher& H) {
 // Calls f(i, key, value, mask) for every i in [s0, s1): the 16-byte aligned body
 // U vectors per thread at a time, the few elements around it by warp 0.
 // `mask` = lanes of the warp calling f together.  HV: also load in_v[i].
-template <typename K, bool HV, int U = 2, typename F>
+// KEEP: the keys are read again soon (an L2 evict_last hint on their loads).
+template <typename K, bool HV, int U = 2, bool KEEP = false, typename F>
 __device__ __forceinline__ void block_for_range(const K* __restrict__ in, const uint32_t* __restrict__ in_v,
                                                 uint64_t s0, uint64_t s1, F&& f) {
     constexpr int VEC = KeyVec<K>::N;
@@ -109,7 +110,8 @@ __device__ __forceinline__ void block_for_range(const K* __restrict__ in, const 
             const uint64_t g = g0 + u * 32 + lane;
             ok[u] = g < nv;
             if (ok[u]) {
-                kv[u] = load_keys16(in + hend + g * VEC);
+                if (KEEP) *reinterpret_cast<uint4*>(&kv[u]) = ld_keep16(in + hend + g * VEC);
+                else kv[u] = load_keys16(in + hend + g * VEC);
                 if (HV) {
                     if (VEC == 4) {
                         const uint4 x = ld_stream16(in_v + hend + g * VEC);
@@ -781,7 +783,8 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
         // a shared counter first.
         const bool heavy = s1 - s0 > STAGE_CAP;
         auto hist = [&](auto fast) {
-            block_for_range<K, false>(in, nullptr, s0, s1, [&](uint64_t, K k, uint32_t, unsigned m) {
+            // (the placement pass reads these keys again: keep them in L2)
+            block_for_range<K, false, 2, true>(in, nullptr, s0, s1, [&](uint64_t, K k, uint32_t, unsigned m) {
                 uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
                 if (j >= nb) {
                     atomicOr(err, DEVERR_BOUNDS);
