@@ -701,7 +701,8 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
             failed = polls >= COPY_WAIT_LIMIT;
             if (cur) phase1 ^= 1; else phase0 ^= 1;
         }
-        if (__syncthreads_or(failed)) break;
+        failed = __syncthreads_or(failed) != 0;  // the same in every thread
+        if (failed) break;
         const uint32_t* s_off = reinterpret_cast<const uint32_t*>(smem + (size_t)cur * BIN_BUF_BYTES);
         const uint32_t k0 = s_k0[cur];
         const bool staged = s_staged[cur] != 0;
@@ -932,7 +933,8 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
             failed = polls >= COPY_WAIT_LIMIT;
             phase ^= 1;
         }
-        if (__syncthreads_or(failed)) break;
+        failed = __syncthreads_or(failed) != 0;  // the same in every thread
+        if (failed) break;
         const uint32_t k0 = s_k0, k1 = s_k1, kofs = s_k0 - s_klo;
         const uint32_t q0 = s_q0, q1 = s_q1;
         // the bin's first queries are loaded now: their latency overlaps the table's build
