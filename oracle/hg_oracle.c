@@ -3,7 +3,8 @@
  *
  * A plain, single-threaded, obviously correct restatement of what the
  * HashGraph build and probe compute (Green et al.'s CSR hash table as used in
- * "Multi-GPU HashGraph", Sec. 3.1 and Algorithm 1; querying in Sec. 3.3).
+ * "Scalable Hash Table for NUMA Systems", the multi-GPU HashGraph: Sec. 3.1
+ * and Algorithm 1; querying in Sec. 3.3).
  * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
  * may load this code.  It shares nothing with the CUDA path: its own hash,
  * its own loops, no headers in common.
