@@ -315,6 +315,14 @@ def test_grouped_hash_join_bins(hg):
     _probe_only(hg, keys, B, queries)
 
 
+def test_grouped_uniform_keys_hash_join_gives_up(hg):
+    # 1024 bins of ~8192 distinct keys each, more than the hash join's table
+    # takes: the first bins overflow, the rest are not tried, and every bin is
+    # answered by the walking probe
+    wl = W.plain_uniform((1 << 23) + 3, (1 << 21) + 9, num_buckets=1 << 23, salt=15)
+    _probe_only(hg, wl.keys, 1 << 23, wl.queries)
+
+
 def test_large_table_few_bins(hg):
     # 2^20 buckets = 128 bins, fewer than the probe's CTAs: the direct probe answers
     # a table larger than L2 (grouping needs several bins per SM)
