@@ -492,6 +492,11 @@ def run_ours(args, rank, world, local_rank):
     isect_probe = (k + 4) * Q + k * N + 4 * (B + 1)
     step_model = build_bytes + walk_probe
     step_model_min = build_bytes + min(walk_probe, isect_probe)
+    # the walk model at the 32-byte sector granularity of the memory system
+    # (diagnostic): queries and counts stream, each offset pair and each walk
+    # outside the long buckets costs the sectors it touches
+    long_bytes = 8 * walk["long_slots"] if flags else k * WL
+    step_model_sector = build_bytes + (k + 4) * Q + 32 * (walk["key_sectors"] + walk["offset_sectors"]) + long_bytes
     per_kernel = {}
     for name, (n_launch, tot_ms) in prof.items():
         if n_launch:
@@ -520,6 +525,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(dom), "peak_kind": peak_kind,
                      "step_model_bytes": step_bytes, "step_model_min_bytes": step_model_min,
+                     "step_model_sector_bytes": step_model_sector,
                      "step_frac": step_model_min / (ms * 1e-3) / 1e9 / peak},
         "kernels": per_kernel,
         "kernel_timing": {"ms_per_step": kernel_run_ms,

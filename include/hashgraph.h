@@ -213,7 +213,9 @@ hg_status hg_long_summary_view(const hg_table* t, const uint32_t** d_n_long, con
  * walks visit (sum of offset[b+1] - offset[b] over slots); d_stats[1] = the
  * part of W in buckets longer than the warp-walk limit (walked by the chunked
  * long-bucket kernel); d_stats[2] = the number of such slots; d_stats[3] =
- * that limit.  d_stats: 4 device uint64_t, overwritten.
+ * that limit; d_stats[4] = the 32-byte sectors the walks of the other slots
+ * touch in the key array; d_stats[5] = the 32-byte sectors of their offset
+ * pairs (offset[b], offset[b+1]).  d_stats: 6 device uint64_t, overwritten.
  */
 hg_status hg_probe_stats(const hg_table* t, const void* d_queries, uint64_t q, uint64_t* d_stats, hg_stream_t s);
 

@@ -293,10 +293,11 @@ def hg_long_summary_view(table: Table):
 
 def hg_probe_stats(table: Table, queries: torch.Tensor, stream=None) -> dict:
     """Walked-length statistics of the byte model (synchronises the stream)."""
-    st = torch.empty(4, dtype=torch.int64, device=queries.device)
+    st = torch.empty(6, dtype=torch.int64, device=queries.device)
     _check(lib.hg_probe_stats(table.handle, _ptr(queries), queries.numel(), _ptr(st), _stream(stream)))
-    w, wl, nl, lim = (int(x) for x in st.cpu().tolist())
-    return {"walked": w, "walked_long": wl, "long_slots": nl, "warp_limit": lim}
+    w, wl, nl, lim, ks, osec = (int(x) for x in st.cpu().tolist())
+    return {"walked": w, "walked_long": wl, "long_slots": nl, "warp_limit": lim, "key_sectors": ks,
+            "offset_sectors": osec}
 
 
 def hg_launch_count() -> int:

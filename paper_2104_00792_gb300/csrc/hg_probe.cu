@@ -555,29 +555,41 @@ cudaError_t run_probe(const Table& t, const K* qs, uint64_t q, void* counts, uin
 }
 
 // Byte-model helper: stats[0] += sum of walked bucket lengths, stats[1] += the
-// part in buckets longer than WALK_WARP, stats[2] += number of such slots.
+// part in buckets longer than WALK_WARP, stats[2] += number of such slots;
+// 32-byte sectors touched by the walks outside long buckets (stats[4]) and by
+// the offset pairs (stats[5]).
 template <typename K>
 __global__ void __launch_bounds__(PROBE_THREADS)
 k_walk_stats(const K* __restrict__ qs, uint64_t q, const uint32_t* __restrict__ offs, Hasher H, uint64_t* stats) {
-    uint64_t w = 0, wl = 0, nl = 0;
+    uint64_t w = 0, wl = 0, nl = 0, ks = 0, os = 0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < q; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t b = bucket_of(qs[i], H);
-        const uint32_t len = offs[b + 1] - offs[b];
+        const uint32_t lo = offs[b], len = offs[b + 1] - lo;
         w += len;
         if (len > WALK_WARP) {
             wl += len;
             nl += 1;
+        } else if (len) {
+            const uint64_t a = (uint64_t)lo * sizeof(K), e = (uint64_t)(lo + len) * sizeof(K);
+            ks += (e + 31) / 32 - a / 32;
         }
+        os += ((uint64_t)b * 4 + 7) / 32 - ((uint64_t)b * 4) / 32 + 1;  // offsets b and b + 1
     }
     const uint64_t a = block_sum(w);
     __syncthreads();
     const uint64_t c = block_sum(wl);
     __syncthreads();
     const uint64_t d = block_sum(nl);
+    __syncthreads();
+    const uint64_t f = block_sum(ks);
+    __syncthreads();
+    const uint64_t g = block_sum(os);
     if (threadIdx.x == 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(stats), (unsigned long long)a);
         atomicAdd(reinterpret_cast<unsigned long long*>(stats + 1), (unsigned long long)c);
         atomicAdd(reinterpret_cast<unsigned long long*>(stats + 2), (unsigned long long)d);
+        atomicAdd(reinterpret_cast<unsigned long long*>(stats + 4), (unsigned long long)f);
+        atomicAdd(reinterpret_cast<unsigned long long*>(stats + 5), (unsigned long long)g);
     }
 }
 
@@ -841,7 +853,7 @@ constexpr uint32_t HJ_MAX_FILL = HJ_SLOTS * 3 / 4;    // distinct keys before th
 constexpr uint32_t HJ_KEY_BYTES = 80 * 1024;          // staged keys (two CTAs per SM)
 constexpr int HJ_THREADS = 512;
 constexpr uint32_t HJ_TRY_LIMIT = 64;                 // fallbacks before the try-rate test applies
-constexpr int HJ_QUNROLL = 8;                         // query loads in flight per thread
+constexpr int HJ_QUNROLL = 4;                         // query loads in flight per thread
 
 // first slot (top 12 bits of a mix of the key) and probe step (odd, so the
 // sequence visits every slot of the power-of-two table)
@@ -1341,7 +1353,7 @@ void gather_release(GatherCtx* ctx, cudaStream_t s) {
 namespace hg {
 
 cudaError_t probe_stats(const Table& t, const void* d_q, uint64_t q, uint64_t* stats, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(stats, 0, 3 * sizeof(uint64_t), s);
+    cudaError_t e = cudaMemsetAsync(stats, 0, 6 * sizeof(uint64_t), s);
     if (e != cudaSuccess) return e;
     const uint64_t lim = WALK_WARP;
     e = cudaMemcpyAsync(stats + 3, &lim, sizeof(lim), cudaMemcpyHostToDevice, s);
