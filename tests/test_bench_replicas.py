@@ -48,3 +48,23 @@ def test_single_process_identity_and_aggregate():
     assert bench.max_over_ranks([3.0, 4.0], None, None) == [3.0, 4.0]
     # 2 replicas x 2^29 keys in 10 ms
     assert bench.aggregate_gkeys(2, 1 << 29, 10.0) == pytest.approx(2 * (1 << 29) / 1e-2 / 1e9)
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the reference arm times the CPU oracle on a bounded sample; no GPU needed
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--log2n", "16",
+                          "--zipf-log2m", "12", "--cpu-sample-log2", "14", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
