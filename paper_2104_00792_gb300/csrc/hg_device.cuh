@@ -176,6 +176,22 @@ __device__ __forceinline__ void note_long(const LongFinder& F, uint32_t b) {
     }
 }
 
+// Index of long bucket b's summary, or SUM_OVERFLOW when it has none usable
+// (not a long bucket, or more distinct keys than a summary holds).
+__device__ __forceinline__ uint32_t summary_index(const LongSummary& S, uint32_t b) {
+    uint32_t h = summary_slot(b, S.map_mask);
+    for (uint32_t probe = 0; probe <= S.map_mask; ++probe) {
+        const unsigned long long w = __ldg(S.map + h);
+        if (w == ~0ull) return SUM_OVERFLOW;
+        if ((uint32_t)w == b) {
+            const uint32_t l = (uint32_t)(w >> 32);
+            return __ldg(S.len + l) <= SUM_SLOTS ? l : SUM_OVERFLOW;
+        }
+        h = (h + 1) & S.map_mask;
+    }
+    return SUM_OVERFLOW;
+}
+
 // Count of `key` in long bucket b from its summary (HG_LONG_SUMMARY): false
 // when the bucket has no summary (too many distinct keys, or none was made),
 // so that the caller walks it instead.

@@ -844,16 +844,22 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
 // cluster and a warp's 32 lookups end together) -- each warp reads 32
 // consecutive keys, and only the first lane of each run of equal keys inserts,
 // with the run's length -- and answers every query with one table lookup: the
-// count of a key in its bin is its count in its bucket.  Items this kernel does
-// not take go to a list for k_probe_bins: slices of bins with very many queries,
-// bins whose keys do not fit, and bins with more distinct keys than the table
-// holds (if most bins are like that, the rest are not tried).
+// count of a key in its bin is its count in its bucket.  A bin whose keys do
+// not fit ("hot": it holds some of the longest buckets) is still taken when the
+// table has long-bucket summaries (HG_LONG_SUMMARY): the CTA finds the bin's
+// buckets of more than SUM_MIN_LEN keys from its offsets, copies only the keys
+// between them, and counts each long bucket from its summary instead.  Items
+// this kernel does not take go to a list for k_probe_bins: bins that do not fit
+// even so (or with more than HJ_MAX_LONG long buckets), and bins with more
+// distinct keys than the table holds (if most bins are like that, the rest are
+// not tried).
 constexpr uint32_t HJ_SLOTS = 4096;                   // table words (32 KiB)
 constexpr uint32_t HJ_MAX_FILL = HJ_SLOTS * 3 / 4;    // distinct keys before the bin falls back
 constexpr uint32_t HJ_KEY_BYTES = 80 * 1024;          // staged keys (two CTAs per SM)
 constexpr int HJ_THREADS = 512;
 constexpr uint32_t HJ_TRY_LIMIT = 64;                 // fallbacks before the try-rate test applies
 constexpr int HJ_QUNROLL = 4;                         // query loads in flight per thread
+constexpr uint32_t HJ_MAX_LONG = 8;                   // long buckets of a hot bin (segments: one more)
 
 // first slot (top 12 bits of a mix of the key) and probe step (odd, so the
 // sequence visits every slot of the power-of-two table)
@@ -871,12 +877,17 @@ __global__ void __launch_bounds__(HJ_THREADS, 2)
 k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_start, BinWork W,
              const uint32_t* __restrict__ keys, const uint32_t* __restrict__ offs, uint64_t B, uint32_t n_keys,
              void* counts, uint64_t* total, uint32_t* work_ctr, uint32_t* fb_list, uint32_t* fb_n, uint32_t* tries,
-             uint32_t* err) {
+             uint32_t* err, LongSummary S) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long* s_ht = reinterpret_cast<unsigned long long*>(smem);
-    const uint32_t* s_keys = reinterpret_cast<const uint32_t*>(smem + HJ_SLOTS * 8);
+    unsigned char* const s_buf = smem + HJ_SLOTS * 8;
+    const uint32_t* s_keys = reinterpret_cast<const uint32_t*>(s_buf);
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ uint32_t s_p, s_k0, s_k1, s_klo, s_q0, s_q1, s_fill, s_abort;
+    __shared__ uint32_t s_p, s_bin, s_k0, s_k1, s_q0, s_q1, s_fill, s_abort, s_hot, s_skip;
+    // the keys to count: segment i is s_keys[s_seg_a[i], + s_seg_n[i]); a hot bin's
+    // long buckets (source range, summary index)
+    __shared__ uint32_t s_nseg, s_seg_a[HJ_MAX_LONG + 1], s_seg_n[HJ_MAX_LONG + 1];
+    __shared__ uint32_t s_nlong, s_long_lo[HJ_MAX_LONG], s_long_hi[HJ_MAX_LONG], s_long_l[HJ_MAX_LONG];
     const unsigned lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t huge_items = *W.huge_chunks;
@@ -891,37 +902,53 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
         while (true) {
             const uint32_t item = atomicAdd(work_ctr, 1u);
             if (item >= n_items) return;
-            bool fb = item < huge_items;
-            uint32_t p = 0, k0 = 0, k1 = 0, q0 = 0, q1 = 0;
-            if (!fb) {
+            uint32_t p, q0, q1;
+            if (item < huge_items) {  // a slice of a bin with very many queries
+                uint32_t lo = 0, hi = *W.n_huge;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (W.huge_chunk_start[mid] <= item) lo = mid; else hi = mid;
+                }
+                p = W.huge_bin[lo];
+                q0 = qbin_start[p] + (item - W.huge_chunk_start[lo]) * W.huge_chunk;
+                q1 = min(qbin_start[p + 1], q0 + W.huge_chunk);
+            } else {
                 p = W.work[item - huge_items];
                 q0 = qbin_start[p];
                 q1 = qbin_start[p + 1];
-                if (q0 == q1) continue;  // no queries in this bin
-                const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
-                const uint64_t b1 = min(B, b0 + BIN_BUCKETS);
-                k0 = min(__ldg(offs + b0), n_keys);
-                k1 = max(k0, min(__ldg(offs + b1), n_keys));
-                const volatile uint32_t* vt = tries;
-                const bool give_up = vt[1] >= HJ_TRY_LIMIT && 2 * vt[1] >= vt[0];
-                fb = give_up || (uint64_t)(k1 - (k0 & ~3u)) * 4 > HJ_KEY_BYTES;
             }
-            if (fb) {
+            if (q0 == q1) continue;  // no queries in this bin
+            const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
+            const uint64_t b1 = min(B, b0 + BIN_BUCKETS);
+            const uint32_t k0 = min(__ldg(offs + b0), n_keys);
+            const uint32_t k1 = max(k0, min(__ldg(offs + b1), n_keys));
+            const volatile uint32_t* vt = tries;
+            const bool give_up = vt[1] >= HJ_TRY_LIMIT && 2 * vt[1] >= vt[0];
+            const uint32_t klo = k0 & ~3u;
+            const bool fits = (uint64_t)(k1 - klo) * 4 <= HJ_KEY_BYTES;
+            if (give_up || (!fits && !S.map)) {
                 fb_list[atomicAdd(fb_n, 1u)] = item;
                 continue;
             }
             atomicAdd(tries, 1u);
-            const uint32_t klo = k0 & ~3u;
-            const uint32_t bytes = ((k1 - klo) * 4 + 15) & ~15u;
             s_p = item;
+            s_bin = p;
             s_k0 = k0;
             s_k1 = k1;
-            s_klo = klo;
             s_q0 = q0;
             s_q1 = q1;
-            fence_proxy_async_smem();  // the key buffer's earlier reads come before the copy's writes
-            mbar_arrive_expect_tx(&s_bar, bytes);
-            if (bytes) bulk_load(smem + HJ_SLOTS * 8, keys + klo, bytes, &s_bar);
+            s_hot = fits ? 0u : 1u;
+            s_skip = 0;
+            s_nlong = 0;
+            if (fits) {  // one segment, copied now (overlapping the current item's queries)
+                const uint32_t bytes = ((k1 - klo) * 4 + 15) & ~15u;
+                s_nseg = 1;
+                s_seg_a[0] = k0 - klo;
+                s_seg_n[0] = k1 - k0;
+                fence_proxy_async_smem();  // the key buffer's earlier reads come before the copy's writes
+                mbar_arrive_expect_tx(&s_bar, bytes);
+                if (bytes) bulk_load(s_buf, keys + klo, bytes, &s_bar);
+            }
             return;
         }
     };
@@ -938,6 +965,98 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
         // here: the table is empty, and the copy of item s_p's keys is in flight
         const uint32_t item = s_p;
         if (item == ~0u) break;
+        const bool hot = s_hot != 0;
+        if (hot) {
+            // a bin too large to copy whole: list its long buckets from its offsets
+            const uint32_t p = s_bin;
+            const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
+            const uint32_t nb = (uint32_t)min((uint64_t)BIN_BUCKETS, B - b0);
+            for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+                const uint32_t hi = min(__ldg(offs + b0 + j + 1), n_keys);
+                const uint32_t lo = min(__ldg(offs + b0 + j), hi);
+                if (hi - lo > SUM_MIN_LEN) {
+                    const uint32_t x = atomicAdd(&s_nlong, 1u);
+                    if (x < HJ_MAX_LONG) {
+                        s_long_lo[x] = lo;
+                        s_long_hi[x] = hi;
+                        s_long_l[x] = (uint32_t)(b0 + j);  // bucket id, then its summary index
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const uint32_t nl = s_nlong;
+                bool ok = nl <= HJ_MAX_LONG;
+                if (ok) {
+                    for (uint32_t a = 1; a < nl; ++a) {  // by position (a few entries)
+                        const uint32_t lo = s_long_lo[a], hi = s_long_hi[a], l = s_long_l[a];
+                        int c = (int)a - 1;
+                        while (c >= 0 && s_long_lo[c] > lo) {
+                            s_long_lo[c + 1] = s_long_lo[c];
+                            s_long_hi[c + 1] = s_long_hi[c];
+                            s_long_l[c + 1] = s_long_l[c];
+                            --c;
+                        }
+                        s_long_lo[c + 1] = lo;
+                        s_long_hi[c + 1] = hi;
+                        s_long_l[c + 1] = l;
+                    }
+                    for (uint32_t a = 0; a < nl && ok; ++a) {
+                        const uint32_t l = summary_index(S, s_long_l[a]);
+                        ok = l != SUM_OVERFLOW;
+                        s_long_l[a] = l;
+                    }
+                }
+                // the keys between the long buckets, each segment copied to a
+                // 16-byte-aligned place in the buffer
+                uint32_t nseg = 0, dst = 0, total = 0, cur = s_k0;
+                for (uint32_t a = 0; a <= nl && ok; ++a) {
+                    const uint32_t e = a < nl ? s_long_lo[a] : s_k1;
+                    if (e > cur) {
+                        const uint32_t al = cur & ~3u;
+                        const uint32_t bytes = ((e - al) * 4 + 15) & ~15u;
+                        ok = dst * 4 + bytes <= HJ_KEY_BYTES;
+                        s_seg_a[nseg] = dst + (cur - al);
+                        s_seg_n[nseg] = e - cur;
+                        ++nseg;
+                        dst += bytes / 4;
+                        total += bytes;
+                    }
+                    if (a < nl) cur = s_long_hi[a];
+                }
+                if (ok) {
+                    s_nseg = nseg;
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&s_bar, total);
+                    cur = s_k0;
+                    dst = 0;
+                    for (uint32_t a = 0; a <= nl; ++a) {
+                        const uint32_t e = a < nl ? s_long_lo[a] : s_k1;
+                        if (e > cur) {
+                            const uint32_t al = cur & ~3u;
+                            const uint32_t bytes = ((e - al) * 4 + 15) & ~15u;
+                            bulk_load(s_buf + dst * 4, keys + al, bytes, &s_bar);
+                            dst += bytes / 4;
+                        }
+                        if (a < nl) cur = s_long_hi[a];
+                    }
+                } else {
+                    s_skip = 1;
+                    fb_list[atomicAdd(fb_n, 1u)] = item;
+                }
+            }
+            __syncthreads();
+            if (s_skip) {  // left to the walking probe: take the next item
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    claim();
+                    s_fill = 0;
+                    s_abort = 0;
+                }
+                __syncthreads();
+                continue;
+            }
+        }
         {
             uint32_t polls = 0;
             while (!mbar_test_parity(&s_bar, phase) && ++polls < COPY_WAIT_LIMIT) {
@@ -947,7 +1066,6 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
         }
         failed = __syncthreads_or(failed) != 0;  // the same in every thread
         if (failed) break;
-        const uint32_t k0 = s_k0, k1 = s_k1, kofs = s_k0 - s_klo;
         const uint32_t q0 = s_q0, q1 = s_q1;
         // the bin's first queries are loaded now: their latency overlaps the table's build
         uint32_t kq[HJ_QUNROLL];
@@ -987,19 +1105,28 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
             len = (above ? (uint32_t)(__ffs(above) - 1) : nv) - lane;
             return head;
         };
-        const uint32_t nk = k1 - k0;
-        for (uint32_t base = warp * 32; base < nk; base += 2 * nwarps * 32) {
-            if (*static_cast<volatile uint32_t*>(&s_abort)) break;
-            const uint32_t base2 = base + nwarps * 32;
-            const uint32_t nv1 = min(32u, nk - base);
-            const uint32_t nv2 = base2 < nk ? min(32u, nk - base2) : 0u;
-            const uint32_t ka = lane < nv1 ? s_keys[kofs + base + lane] : 0u;
-            const uint32_t kb = lane < nv2 ? s_keys[kofs + base2 + lane] : 0u;
-            uint32_t la, lb;
-            const bool ha = runs(nv1, ka, la);
-            const bool hb = runs(nv2, kb, lb);
-            if (ha) insert(ka, la);
-            if (hb) insert(kb, lb);
+        const uint32_t nseg = s_nseg;
+        for (uint32_t sg = 0; sg < nseg; ++sg) {
+            const uint32_t kofs = s_seg_a[sg], nk = s_seg_n[sg];
+            for (uint32_t base = warp * 32; base < nk; base += 2 * nwarps * 32) {
+                if (*static_cast<volatile uint32_t*>(&s_abort)) break;
+                const uint32_t base2 = base + nwarps * 32;
+                const uint32_t nv1 = min(32u, nk - base);
+                const uint32_t nv2 = base2 < nk ? min(32u, nk - base2) : 0u;
+                const uint32_t ka = lane < nv1 ? s_keys[kofs + base + lane] : 0u;
+                const uint32_t kb = lane < nv2 ? s_keys[kofs + base2 + lane] : 0u;
+                uint32_t la, lb;
+                const bool ha = runs(nv1, ka, la);
+                const bool hb = runs(nv2, kb, lb);
+                if (ha) insert(ka, la);
+                if (hb) insert(kb, lb);
+            }
+        }
+        if (hot && warp < s_nlong) {  // a long bucket's distinct keys with their counts
+            const uint32_t l = s_long_l[warp];
+            const uint32_t n = __ldg(S.len + l);
+            const uint32_t* sk = static_cast<const uint32_t*>(S.keys) + (size_t)l * SUM_SLOTS;
+            for (uint32_t e = lane; e < n; e += 32) insert(__ldg(sk + e), __ldg(S.cnt + (size_t)l * SUM_SLOTS + e));
         }
         __syncthreads();
         const bool abort = s_abort != 0;
@@ -1079,7 +1206,7 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
             per_sm = 1;
         launch_begin("probe_hash", s);
         kern<<<num_sms() * per_sm, HJ_THREADS, smem, s>>>(qs, g.bin_start, g.items, keys, t.offsets, t.B, (uint32_t)t.n,
-                                                          counts, total, ctrs, fb_list, ctrs + 2, ctrs + 3, t.err);
+                                                          counts, total, ctrs, fb_list, ctrs + 2, ctrs + 3, t.err, t.sum);
         launch_end("probe_hash", s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -7,7 +7,9 @@ the oracle.
   slots; every such bucket is listed exactly once, and no other bucket.
 * Counts, totals and join counts are bit-exact with the oracle's, for tables
   with and without summaries, through the direct and the grouped probe; the
-  grouped cases include bins holding more queries than one work item takes.
+  grouped cases include bins holding more queries than one work item takes,
+  and bins too large to copy whole that the hash join takes through their
+  long buckets' summaries (or leaves to the walking probe).
 
 Zipf-weighted queries (each value queried in proportion to its copies) make
 the oracle's walk quadratic, so its counts are taken once per distinct query
@@ -171,3 +173,35 @@ def test_zipf_weighted_direct(hg):
     # a table that stays in L2 with many queries: the direct probe
     wl = W.zipf_weighted(n=1 << 21, num_buckets=1 << 20, q=(1 << 21) + 1, M=1 << 14, salt=66)
     _run(hg, wl.keys, 1 << 20, wl.queries, hg.HG_LONG_SUMMARY, expect_summaries=True)
+
+
+def _keys_in_bucket(b, B, count, start):
+    """`count` distinct 32-bit keys whose bucket is b, searched upward from `start`."""
+    out, x = [], start
+    while len(out) < count:
+        cand = (np.arange(x, x + (1 << 25), dtype=np.uint64) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+        out.extend(cand[oracle.buckets(cand, B, 0) == b].tolist())
+        x += 1 << 25
+    return np.array(out[:count], dtype=np.uint32)
+
+
+def test_hash_join_hot_bins(hg):
+    # 1024 bins; bins holding long buckets are too large to copy whole, so the
+    # hash join copies only the keys between their long buckets and takes the
+    # long buckets' counts from their summaries.  Three bins are built to
+    # defeat it and go to the walking probe: bin 5 with nine long buckets, bin 9
+    # with a long bucket of 80 distinct keys (no summary), bin 11 with more
+    # short-bucket keys than the buffer holds.
+    B = 1 << 23
+    wl = W.zipf_large(n=1 << 23, num_buckets=B, q=(1 << 21) + 5, M=1 << 16, salt=70)
+    rng = np.random.default_rng(71)
+    cand = rng.integers(0, 1 << 32, size=1 << 25, dtype=np.uint64).astype(np.uint32)
+    bins = oracle.buckets(cand, B, 0) >> 13
+    in5 = np.unique(cand[bins == 5])[:9]
+    in11 = cand[bins == 11][:30000]
+    k9 = _keys_in_bucket((9 << 13) + 77, B, 80, start=12345)
+    keys = np.concatenate([wl.keys, np.repeat(in5, 9000), np.repeat(k9, 250), in11])
+    keys = keys[rng.permutation(keys.size)]
+    queries = np.concatenate([in5, k9, in11[:5000], wl.queries])
+    for flags in (hg.HG_LONG_SUMMARY, 0):
+        _run(hg, keys, B, queries, flags, expect_summaries=True if flags else None)
