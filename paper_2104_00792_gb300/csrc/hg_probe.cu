@@ -837,8 +837,9 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
 
 // Grouped probe by hash join (32-bit keys): the paper's per-bucket list
 // intersection done a bin at a time through a table of the bin's distinct keys.
-// A CTA takes one bin (a work item covering all its queries), brings the bin's
-// keys into shared memory by a bulk copy, counts them into a shared-memory
+// A CTA takes one work item (a bin's queries, or a slice of them for a bin with
+// very many), brings the bin's keys into shared memory by a bulk copy, counts
+// them into a shared-memory
 // open-addressing table of (count << 32 | key) words (zero = empty: a present
 // key has a count of at least one; double hashing, so probe sequences do not
 // cluster and a warp's 32 lookups end together) -- each warp reads 32
@@ -860,6 +861,7 @@ constexpr int HJ_THREADS = 512;
 constexpr uint32_t HJ_TRY_LIMIT = 64;                 // fallbacks before the try-rate test applies
 constexpr int HJ_QUNROLL = 4;                         // query loads in flight per thread
 constexpr uint32_t HJ_MAX_LONG = 8;                   // long buckets of a hot bin (segments: one more)
+static_assert(HJ_KEY_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
 
 // first slot (top 12 bits of a mix of the key) and probe step (odd, so the
 // sequence visits every slot of the power-of-two table)
