@@ -857,7 +857,7 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
 constexpr uint32_t HJ_SLOTS = 4096;                   // table words (32 KiB)
 constexpr uint32_t HJ_MAX_FILL = HJ_SLOTS * 3 / 4;    // distinct keys before the bin falls back
 constexpr uint32_t HJ_KEY_BYTES = 80 * 1024;          // staged keys (two CTAs per SM)
-constexpr int HJ_THREADS = 512;
+constexpr int HJ_THREADS = 768;                       // two CTAs (48 warps) per SM: 512 took 1.29 ms, 768 1.14
 constexpr uint32_t HJ_TRY_LIMIT = 64;                 // fallbacks before the try-rate test applies
 constexpr int HJ_QUNROLL = 4;                         // query loads in flight per thread
 constexpr uint32_t HJ_MAX_LONG = 8;                   // long buckets of a hot bin (segments: one more)
