@@ -1207,7 +1207,7 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
     const size_t o_cnt = off; off += al((size_t)P * 4);
-    const size_t o_ctr = off; off += al(64);
+    off += al(64);  // (spare, zeroed with the counts)
     const size_t zero_bytes = off;
     const size_t o_ca = off; off += al((size_t)nch_a * RADIX * 4);
     const size_t o_cb = off; off += al(two ? (size_t)nch_b_max * RADIX * 4 : 0);
