@@ -377,6 +377,15 @@ hg_status hg_server_free(hg_server* s);
  */
 hg_status hg_selftest_bounded_wait(hg_stream_t s);
 
+/*
+ * hg_debug_fail_alloc_after -- test hook, host-side fault injection: with
+ * n >= 0 the library's device allocations after the next n fail as if the
+ * device were out of memory (the calls return HG_ERR_OOM after releasing what
+ * they had allocated, and launch nothing on the missing memory); n < 0 turns
+ * the injection off.  Process-wide; for tests, not for concurrent use.
+ */
+void hg_debug_fail_alloc_after(int64_t n);
+
 /* Number of kernels this process has launched through the library so far. */
 uint64_t hg_launch_count(void);
 

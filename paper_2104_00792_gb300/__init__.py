@@ -68,6 +68,8 @@ lib.hg_table_view.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), cty
 lib.hg_probe_stats.argtypes = [_vp, _vp, _u64, _vp, _vp]
 lib.hg_long_summary_view.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 5 + [ctypes.POINTER(ctypes.c_uint32)] * 2
 lib.hg_long_summary_view.restype = ctypes.c_int
+lib.hg_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
+lib.hg_debug_fail_alloc_after.restype = None
 lib.hg_selftest_bounded_wait.argtypes = [_vp]
 lib.hg_selftest_bounded_wait.restype = ctypes.c_int
 lib.hg_launch_count.restype = _u64
@@ -289,6 +291,12 @@ def hg_long_summary_view(table: Table):
     return {"n_long": arr(ptrs[0], 1, "<i4"), "bucket": arr(ptrs[1], c, "<i4"), "len": arr(ptrs[2], c, "<i4"),
             "keys": arr(ptrs[3], c * sl, "<i4" if table.key_bytes == 4 else "<i8"),
             "counts": arr(ptrs[4], c * sl, "<i4"), "cap": c, "slots": sl}
+
+
+def hg_debug_fail_alloc_after(n: int) -> None:
+    """Test hook: the library's device allocations after the next n fail as if
+    the device were out of memory (n < 0: off)."""
+    lib.hg_debug_fail_alloc_after(int(n))
 
 
 def hg_probe_stats(table: Table, queries: torch.Tensor, stream=None) -> dict:

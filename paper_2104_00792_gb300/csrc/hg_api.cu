@@ -110,7 +110,15 @@ int num_sms() {
     return cached[dev];
 }
 
+// hg_debug_fail_alloc_after: allocations left before injected failures (< 0: off)
+std::atomic<int64_t> g_allocs_before_failure{-1};
+
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    for (int64_t k = g_allocs_before_failure.load(); k >= 0;) {
+        if (k == 0) return cudaErrorMemoryAllocation;  // injected (host side; nothing runs on the device)
+        if (g_allocs_before_failure.compare_exchange_weak(k, k - 1)) break;
+    }
     static std::once_flag once[64];
     int dev = 0;
     cudaGetDevice(&dev);
@@ -425,6 +433,8 @@ hg_status hg_long_summary_view(const hg_table* ht, const uint32_t** d_n_long, co
     if (slots) *slots = SUM_SLOTS;
     return HG_OK;
 }
+
+void hg_debug_fail_alloc_after(int64_t n) { g_allocs_before_failure.store(n < 0 ? -1 : n); }
 
 hg_status hg_selftest_bounded_wait(hg_stream_t s) {
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
