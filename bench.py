@@ -15,6 +15,14 @@ between steps.  Multi-GPU runs (torchrun) are independent replicas: every
 rank builds and probes its own table (weak scaling; no collective on the data
 path).  `--impl reference` times the CPU oracle (the only reference this
 method has) on a bounded sample of the same workload.
+
+With no --workload the line also carries, under "workloads", the other
+configurations measured in the same run (each reduced where stated): the
+2^20 uniform table (L2-resident, flushed between steps), the 64-bit
+key-value join (2^27 pairs, join count and gather), the batch of 4096 tables
+in one graph-replayed launch, and the served request stream (p50/p99 against
+the one-request-at-a-time path, every probe compared with it and a seeded 1%
+sample with the oracle).
 """
 from __future__ import annotations
 
@@ -66,6 +74,12 @@ def parse():
     p.add_argument("--budget-gb", type=float, default=100.0, help="serving: device-memory budget for tables")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
     p.add_argument("--no-plain", action="store_true", help="batched: skip the one-launch-per-table comparison")
+    p.add_argument("--only-headline", action="store_true",
+                   help="zipf_large: skip the other configurations measured under \"workloads\"")
+    p.add_argument("--sub-requests", type=int, default=50_000,
+                   help="serving stream length when measured beside the headline (the first requests of the "
+                        "200,000-request stream)")
+    p.add_argument("--no-verify", action="store_true", help="serving: skip the result checks")
     return p.parse_args()
 
 
@@ -189,9 +203,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+def ncu_traffic_rows():
+    """The committed ncu DRAM-traffic summary of the headline step as a dict, if
+    it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic_zipf_large.txt")
     try:
         rows = {}
@@ -204,8 +218,37 @@ def ncu_traffic(kernel):
         return None
     if rows.get("source_hash") != source_hash():
         return None
-    v = rows.get(f"traffic_bytes_per_launch.{kernel}")
+    return rows
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary (None
+    when it is missing or was taken on other kernel sources)."""
+    rows = ncu_traffic_rows()
+    v = rows.get(f"traffic_bytes_per_launch.{kernel}") if rows else None
     return float(v) if v else None
+
+
+def step_traffic(per_kernel, steps):
+    """ncu DRAM bytes of one whole step: every kernel's per-launch traffic times
+    its launches per step.  Kernels the capture has no row for are counted at
+    their model bytes and listed; kernels with neither are listed as skipped."""
+    rows = ncu_traffic_rows()
+    if not rows:
+        return None, None
+    total, at_model, skipped = 0.0, [], []
+    for name, v in per_kernel.items():
+        tr = rows.get(f"traffic_bytes_per_launch.{name}")
+        if tr is not None:
+            tr = float(tr)
+        elif v.get("model_bytes"):
+            tr = float(v["model_bytes"])
+            at_model.append(name)
+        else:
+            skipped.append(name)
+            continue
+        total += tr * v["launches"] / steps
+    return total, {"at_model_bytes": at_model, "skipped": skipped}
 
 
 def batch_traffic_ratio():
@@ -226,6 +269,32 @@ def batch_traffic_ratio():
     return float(v) if v else None
 
 
+def host_cpu():
+    """The host's CPU model and core count (for the CPU baseline's record)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if not model.isdigit():
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model or platform.processor() or "unknown", "machine": platform.machine(),
+            "nproc": os.cpu_count()}
+
+
 def cpu_oracle_sample(wl, log2s):
     """Oracle build + count on the first 2^log2s keys and queries of the
     workload, table size scaled to keep the same keys-per-bucket ratio."""
@@ -241,8 +310,10 @@ def cpu_oracle_sample(wl, log2s):
     t.query_count(queries)
     dt = time.perf_counter() - t0
     return {"value": (2 * n) / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first 2^{log2s} keys and 2^{log2s} queries of the workload, B={B} (same keys/bucket), "
-                      f"build+count, {dt:.2f} s single-threaded"}
+            "sample": f"first 2^{log2s} keys and 2^{log2s} queries of the workload (of 2^{wl.keys.size.bit_length() - 1} "
+                      f"each); B scaled with the sample, {wl.num_buckets} x 2^{log2s} / {wl.keys.size} = {B} buckets, "
+                      f"so keys per bucket stay as in the full workload; build+count, {dt:.2f} s on one thread",
+            "host": host_cpu()}
 
 
 def run_reference(args, rank, world):
@@ -497,6 +568,9 @@ def run_ours(args, rank, world, local_rank):
     # outside the long buckets costs the sectors it touches
     long_bytes = 8 * walk["long_slots"] if flags else k * WL
     step_model_sector = build_bytes + (k + 4) * Q + 32 * (walk["key_sectors"] + walk["offset_sectors"]) + long_bytes
+    # the method's algorithmic bytes as the survey's measurement section states them:
+    # build (3k + 2v) N + 16 B, probe (k + 12) Q + k W, W = every key every query walks
+    step_model_alg = build_bytes + (k + 12) * Q + k * W
     per_kernel = {}
     for name, (n_launch, tot_ms) in prof.items():
         if n_launch:
@@ -505,6 +579,7 @@ def run_ours(args, rank, world, local_rank):
     tot = sum(v["ms_per_launch"] * v["launches"] for v in per_kernel.values()) or 1.0
     for v in per_kernel.values():
         v["share"] = v["ms_per_launch"] * v["launches"] / tot
+    traffic_total, traffic_note = step_traffic(per_kernel, args.steps)
     dom = max((n for n in per_kernel if n in model), key=lambda n: per_kernel[n]["share"])
     d = per_kernel[dom]
     achieved = model[dom] / (d["ms_per_launch"] * 1e-3) / 1e9
@@ -524,6 +599,10 @@ def run_ours(args, rank, world, local_rank):
                    [args.query_form]},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(dom), "peak_kind": peak_kind,
+                     "step_frac_alg": step_model_alg / (ms * 1e-3) / 1e9 / peak,
+                     "step_model_alg_bytes": step_model_alg,
+                     "step_model_alg": "(3k+2v)N + 16B + (k+12)Q + kW, k=4, v=0, W=walk.walked",
+                     "traffic_total": traffic_total, "traffic_total_note": traffic_note,
                      "step_model_bytes": step_bytes, "step_model_min_bytes": step_model_min,
                      "step_model_sector_bytes": step_model_sector,
                      "step_frac": step_model_min / (ms * 1e-3) / 1e9 / peak},
@@ -543,6 +622,27 @@ def run_ours(args, rank, world, local_rank):
                        "pipelining": "copies on their own streams, two device buffer sets alternating"}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(wl, cpu_sample_log2(args))
+    if world == 1 and not args.only_headline and not weighted:
+        # the other configurations, measured in the same run (one GPU; each with its own checks)
+        del keys, queries, counts, total, wl
+        torch.cuda.empty_cache()
+        subs = {}
+        jobs = (("plain_small", lambda: measure_plain_small(args, dev)),
+                ("join_kv", lambda: measure_join(args, dev, with_oracle=not args.no_cpu)),
+                ("batched", lambda: measure_batched(args, dev, args.tables)),
+                ("serving", lambda: measure_serving(args, dev, args.sub_requests, verify=not args.no_verify)))
+        for name, fn in jobs:
+            t0 = time.perf_counter()
+            try:
+                subs[name] = fn()
+            except Exception as exc:  # the headline line is still printed
+                subs[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            subs[name]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
+        if "requests" in subs["serving"]:
+            subs["serving"]["reduction"] = (f"the first {args.sub_requests} requests of the 200,000-request stream "
+                                            f"(python bench.py --workload serving runs all of them)")
+        line["workloads"] = subs
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -557,25 +657,23 @@ def batch_desc(tables):
             f"persistent launch replayed from a CUDA graph")
 
 
-def run_batched(args, rank, world, local_rank):
-    """Config: thousands of small tables of uneven size built and probed together."""
+def measure_batched(args, dev, tables, salt=0, with_e2e=True, with_plain=True, dist=None):
+    """Thousands of small tables of uneven size built and probed in one
+    persistent launch (replayed from a CUDA graph).  Returns the measurement as
+    a dict (value, roofline, the one-launch-per-table comparison, e2e, checks)."""
     import numpy as np
     import torch
 
+    import oracle
     import paper_2104_00792_gb300 as hg
     import workloads as W
 
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    wl = W.batched_uniform(args.tables, 8, 20, salt=rank)
+    wl = W.batched_uniform(tables, 8, 20, salt=salt)
     N, Q = wl.keys.size, wl.queries.size
     keys = torch.from_numpy(wl.keys.view(np.int32)).to(dev)
     queries = torch.from_numpy(wl.queries.view(np.int32)).to(dev)
     counts = torch.empty(Q, dtype=torch.int32, device=dev)
+    prev_stream = torch.cuda.current_stream(dev)
     stream = torch.cuda.Stream(dev)  # a stream of its own: the run is captured once and replayed as a graph
     torch.cuda.synchronize(dev)
     torch.cuda.set_stream(stream)
@@ -585,8 +683,9 @@ def run_batched(args, rank, world, local_rank):
         hg.hg_batch_run(b, keys, queries, counts, stream=stream)
     walked = hg.hg_batch_walk_stats(b, queries, stream=stream)
     torch.cuda.synchronize(dev)
+    steps = max(args.steps, 3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0)
+    sampler = ClockSampler(dev.index if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0)
     with sampler:
         time.sleep(0.3)
         if dist is not None:
@@ -594,17 +693,17 @@ def run_batched(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         launches0 = hg.hg_launch_count()
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             hg.hg_batch_run(b, keys, queries, counts, stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         launches = hg.hg_launch_count() - launches0
-        ms = ev0.elapsed_time(ev1) / args.steps
+        ms = ev0.elapsed_time(ev1) / steps
         # end to end through the C ABI with host buffers: pinned keys and queries
         # copied in, counts copied out, every step; copies on their own streams,
         # two buffer sets (and two batch plans) alternating
         e2e_ms = None
-        if not args.no_e2e:
+        if with_e2e:
             h_keys = torch.from_numpy(wl.keys.view(np.int32)).pin_memory()
             h_q = torch.from_numpy(wl.queries.view(np.int32)).pin_memory()
             b2 = hg.hg_batch_create(wl.key_offsets, wl.num_buckets, wl.query_offsets, stream=stream)
@@ -639,7 +738,7 @@ def run_batched(args, rank, world, local_rank):
             for k in range(2):
                 e2e_step(k)
             torch.cuda.synchronize(dev)
-            e_steps = max(4, args.steps // 3)
+            e_steps = max(4, steps // 3)
             ev0.record(stream)
             s_in.wait_event(ev0)
             for k in range(e_steps):
@@ -655,10 +754,22 @@ def run_batched(args, rank, world, local_rank):
     if e2e_ms is not None:
         e2e_ms = e2e_v
     hg.hg_batch_sync(b, stream=stream)
-    ok = True
+    got = counts.cpu().numpy().view(np.uint32)
+    # seeded sample of tables against the oracle (their offsets and every count)
+    rng = np.random.default_rng(0x2104)
+    sample = sorted(set(rng.choice(wl.n_tables, size=min(16, wl.n_tables), replace=False).tolist())
+                    | {int(np.argmax(wl.num_buckets))})
+    oracle_ok = True
+    for t in sample:
+        k_t, B_t, q_t = wl.table(t)
+        ref = oracle.build_table(np.ascontiguousarray(k_t), B_t, 0)
+        o, _ = hg.hg_batch_view(b, t)
+        q0, q1 = int(wl.query_offsets[t]), int(wl.query_offsets[t + 1])
+        oracle_ok &= bool(np.array_equal(o.cpu().numpy().view(np.uint32).astype(np.uint64), ref.offsets))
+        oracle_ok &= bool(np.array_equal(got[q0:q1].astype(np.uint64), ref.query_count(np.ascontiguousarray(q_t))))
     # the same tables one launch sequence per table (the plain path), for comparison
-    plain_ms = None
-    if not args.no_plain and rank == 0:
+    plain_ms, same = None, None
+    if with_plain:
         c2 = torch.empty(Q, dtype=torch.int32, device=dev)
 
         def plain_step():
@@ -676,39 +787,60 @@ def run_batched(args, rank, world, local_rank):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         plain_ms = ev0.elapsed_time(ev1)
-        ok = bool(torch.equal(c2, counts))
+        same = bool(torch.equal(c2, counts))
     b.free(stream)
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return
+    torch.cuda.synchronize(dev)
+    torch.cuda.set_stream(prev_stream)
     peak, peak_kind = measured_peak()
     B = int(wl.num_buckets.sum())
     model = 12 * N + 16 * B + 16 * Q + 4 * walked   # build (3k N + 16 B) + probe (k Q + 8 Q + 4 Q + k W), k = 4
     achieved = model / (ms * 1e-3) / 1e9
     clocks = sampler.summary()
-    line = {
-        "metric": BATCH_METRIC, "value": aggregate_gkeys(world, N + Q, ms), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": batch_desc(args.tables), "parallelism": f"replicas{world}",
-                   "keys": N, "queries": Q, "buckets": B, "params": chosen,
+    ratio = batch_traffic_ratio()
+    out = {
+        "value": aggregate_gkeys(1 if dist is None else dist.get_world_size(), N + Q, ms), "unit": UNIT,
+        "ms_per_step": ms, "steps": steps,
+        "config": {"workload": batch_desc(tables), "keys": N, "queries": Q, "buckets": B, "params": chosen,
                    "l2": f"inputs exceed L2 ({(N + Q) * 4 / 2**30:.1f} GiB read per step); no flush"},
         "roofline": {"bound": "hbm", "kernel": "batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": (batch_traffic_ratio() * model) if batch_traffic_ratio() else None,
+                     "frac": achieved / peak, "traffic": (ratio * model) if ratio else None,
                      "traffic_note": "ncu DRAM bytes per algorithmic byte at 512 tables x this batch's model bytes",
                      "peak_kind": peak_kind, "model_bytes": model},
         "vs_plain": {"plain_ms_per_step": plain_ms, "speedup": (plain_ms / ms) if plain_ms else None,
                      "plain": "hg_build + hg_query_count + hg_free per table, same stream",
-                     "counts_identical": ok},
+                     "counts_identical": same},
+        "check": {"oracle_tables": len(sample), "oracle_equal": oracle_ok},
         "gpu_launches": launches,
         "clocks": {k2: clocks[k2] for k2 in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
     if e2e_ms is not None:
-        line["e2e"] = {"value": aggregate_gkeys(world, N + Q, e2e_ms), "unit": UNIT,
-                       "h2d_bytes_per_step": 4 * (N + Q), "d2h_bytes_per_step": 4 * Q, "ms_per_step": e2e_ms}
-    print(json.dumps(line), flush=True)
+        out["e2e"] = {"value": aggregate_gkeys(1 if dist is None else dist.get_world_size(), N + Q, e2e_ms),
+                      "unit": UNIT, "h2d_bytes_per_step": 4 * (N + Q), "d2h_bytes_per_step": 4 * Q,
+                      "ms_per_step": e2e_ms}
+    return out
+
+
+def run_batched(args, rank, world, local_rank):
+    """Config: thousands of small tables of uneven size built and probed together."""
+    import torch
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    m = measure_batched(args, dev, args.tables, salt=rank, with_e2e=not args.no_e2e,
+                        with_plain=not args.no_plain and rank == 0, dist=dist)
+    if rank == 0:
+        line = {"metric": BATCH_METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": m["steps"],
+                "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": dict(m["config"], parallelism=f"replicas{world}")}
+        line.update({k: m[k] for k in ("roofline", "vs_plain", "check", "gpu_launches", "clocks") if k in m})
+        if "e2e" in m:
+            line["e2e"] = m["e2e"]
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -722,25 +854,29 @@ def serve_desc(n, load, budget_gb):
             f"from the target's keys) on tables resident under an arrival-order LRU with a {budget_gb:g} GB budget")
 
 
-def run_serving(args, rank, world, local_rank):
-    """Config: a request stream served by the engine, against one request at a time."""
+def measure_serving(args, dev, nreq, verify=True):
+    """A request stream served by the engine, against one request at a time on
+    one stream (the plain path).  Latency runs at the calibrated arrival rate,
+    capacity runs with every request available; with `verify`, a further run of
+    each path fingerprints every probe's counts on the device (all compared),
+    and a seeded 1% of the probes is answered by the oracle."""
     import numpy as np
     import torch
 
     import paper_2104_00792_gb300 as hg
     import workloads as W
 
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    if rank != 0:  # one GPU per stream; replicas would serve independent streams
-        return
     budget = int(args.budget_gb * 1e9)
-    trace = W.serving_trace(args.requests, budget_bytes=budget, salt=rank)
+    trace = W.serving_trace(nreq, budget_bytes=budget, salt=0)
     n_of = W.serve_table_n(trace)
-    nreq = len(trace)
     stream = torch.cuda.current_stream(dev)
     sid = stream.cuda_stream
     gaps = np.array([r.gap for r in trace], dtype=np.float64)
+    probe_idx = [i for i in range(nreq) if trace[i].kind == "probe"]
+    rng = np.random.default_rng(0x2104)
+    o_sample = set(rng.choice(probe_idx, size=max(1, len(probe_idx) // 100), replace=False).tolist()) \
+        if probe_idx else set()
+    ar = torch.arange(1, (1 << 22) + 2, dtype=torch.int64, device=dev)
 
     def make_inputs(r):
         if r.kind == "build":
@@ -752,16 +888,18 @@ def run_serving(args, rank, world, local_rank):
         c = torch.empty(max(r.size, 1), dtype=torch.int32, device=dev)
         return q[: r.size], c[: r.size]
 
-    sample = {i for i in range(nreq) if trace[i].kind == "probe" and i % 97 == 0}
+    def fingerprint(c):
+        # (sum of counts, sum of (slot + 1) x count), both mod 2^64: every slot's count enters
+        c64 = c.to(torch.int64)
+        return torch.stack([c64.sum(), (c64 * ar[: c.numel()]).sum()])
 
-    def plain_run(arrivals, limit=None):
+    def plain_run(arrivals, limit=None, fps=None):
         """One request at a time on one stream, tables kept under the same LRU."""
         from collections import OrderedDict
         tables = OrderedDict()
         used = 0
-        done = np.zeros(nreq)
-        keep = {}
         m = nreq if limit is None else limit
+        done = np.zeros(m)
         t0 = time.perf_counter()
         for i in range(m):
             r = trace[i]
@@ -772,9 +910,9 @@ def run_serving(args, rank, world, local_rank):
             if r.kind == "build":
                 need = hg.hg_server_table_bytes(r.size, r.size)
                 while used + need > budget and tables:
-                    _, (tb, b) = tables.popitem(last=False)
+                    _, (tb, bb) = tables.popitem(last=False)
                     tb.free(stream)
-                    used -= b
+                    used -= bb
                 tables[r.table] = (hg.hg_build(a, r.size, 0, stream=stream), need)
                 used += need
             else:
@@ -782,19 +920,18 @@ def run_serving(args, rank, world, local_rank):
                 hg.hg_query_count(tables[r.table][0], a, c, None, stream=stream)
             stream.synchronize()
             done[i] = time.perf_counter() - t0
-            if i in sample:
-                keep[i] = c.clone()
+            if fps is not None and c is not None:
+                fps[i] = fingerprint(c)
         for tb, _ in tables.values():
             tb.free(stream)
         torch.cuda.synchronize(dev)
-        return done[:m], keep
+        return done
 
-    def engine_run(arrivals, window=None):
+    def engine_run(arrivals, window=None, fps=None, keep=None):
         """Requests submitted at their arrival times (or, with `window`, as soon
         as fewer than `window` are outstanding: the engine's capacity)."""
         srv = hg.Server(budget, max_batch=256)
         done = np.zeros(nreq)
-        keep = {}
         live = {}
         i = 0
         t0 = time.perf_counter()
@@ -816,30 +953,63 @@ def run_serving(args, rank, world, local_rank):
                 done[j] = time.perf_counter() - t0
                 if st != hg.HG_OK:
                     raise RuntimeError(f"request {j} failed with status {st}")
-                if j in sample:
-                    keep[j] = c
+                if fps is not None and c is not None:
+                    fps[j] = fingerprint(c)
+                if keep is not None and j in o_sample:
+                    keep[j] = c.cpu().numpy().view(np.uint32).copy()
         stats = srv.stats()
         srv.free()
         torch.cuda.synchronize(dev)
-        return done, keep, stats
+        return done, stats
 
     # capacity of the plain path: its mean service time over the first requests, back to back
     n_cal = min(nreq, 3000)
-    cal_done, _ = plain_run(None, limit=n_cal)
+    cal_done = plain_run(None, limit=n_cal)
     service = float(cal_done[-1]) / n_cal
     rate = args.load / service
     arrivals = np.cumsum(gaps) / rate
     arrivals -= arrivals[0]
-    e_done, e_keep, e_stats = engine_run(arrivals)
-    p_done, p_keep = plain_run(arrivals)
-    same = all(torch.equal(e_keep[i], p_keep[i]) for i in sample)
+    launches0 = hg.hg_launch_count()
+    e_done, e_stats = engine_run(arrivals)
+    e_launches = hg.hg_launch_count() - launches0
+    p_done = plain_run(arrivals)
     keys_total = sum(r.size for r in trace)
     # capacity: every request available at once (the engine keeps 64 outstanding)
-    cap_e, _, _ = engine_run(np.zeros(nreq), window=64)
-    cap_p, _ = plain_run(None)
+    cap_e, _ = engine_run(np.zeros(nreq), window=64)
+    cap_p = plain_run(None)
     capacity = {"engine_gkeys_per_s": keys_total / float(cap_e.max()) / 1e9,
                 "plain_gkeys_per_s": keys_total / float(cap_p.max()) / 1e9}
     capacity["ratio"] = capacity["engine_gkeys_per_s"] / capacity["plain_gkeys_per_s"]
+
+    check = None
+    if verify:
+        import oracle
+        fe, fp, keep = {}, {}, {}
+        engine_run(np.zeros(nreq), window=64, fps=fe, keep=keep)
+        plain_run(None, fps=fp)
+        same_all = len(fe) == len(fp) == len(probe_idx) and all(torch.equal(fe[i], fp[i]) for i in probe_idx)
+        # the oracle on the seeded sample: each sampled probe's table regenerated on
+        # the host and built by the oracle (one table at a time)
+        by_table = {}
+        for i in sorted(o_sample):
+            by_table.setdefault(trace[i].table, []).append(i)
+        o_equal, o_slots = True, 0
+        t0 = time.perf_counter()
+        for t, idx in by_table.items():
+            n = n_of[t]
+            hk = W.uniform_u32(trace[idx[0]].key_state, n)
+            ref = oracle.build_table(hk, n, 0)
+            for i in idx:
+                r = trace[i]
+                want = ref.query_count(W.probe_mix(hk, r.size, 0.6, r.sel, r.miss))
+                o_equal &= bool(np.array_equal(keep[i][: r.size].astype(np.uint64), want))
+                o_slots += r.size
+            del ref, hk
+        check = {"probes": len(probe_idx), "all_probes_engine_equals_plain": bool(same_all),
+                 "compare": "per-probe device fingerprints (sum of counts, sum of (slot+1) x count, mod 2^64) of "
+                            "every probe, engine (window 64) vs plain; the oracle sample compares every count",
+                 "oracle_sample_probes": len(o_sample), "oracle_sample_slots": o_slots,
+                 "oracle_sample_equal": bool(o_equal), "oracle_s": time.perf_counter() - t0}
 
     def summary(done):
         lat = (done - arrivals) * 1e3
@@ -848,20 +1018,187 @@ def run_serving(args, rank, world, local_rank):
                 "mean_ms": float(lat.mean()), "gkeys_per_s": keys_total / span / 1e9, "makespan_s": span}
 
     eng, pla = summary(e_done), summary(p_done)
+    return {"p50_ms": eng["p50_ms"], "p99_ms": eng["p99_ms"], "plain_p50_ms": pla["p50_ms"],
+            "plain_p99_ms": pla["p99_ms"], "load": args.load, "gkeys": eng["gkeys_per_s"],
+            "plain_gkeys": pla["gkeys_per_s"], "requests": nreq,
+            "config": {"workload": serve_desc(nreq, args.load, args.budget_gb), "rate_per_s": rate,
+                       "plain_service_ms": service * 1e3, "calibration_requests": n_cal},
+            "engine": eng, "plain": pla,
+            "vs_plain": {"p50": pla["p50_ms"] / eng["p50_ms"], "p99": pla["p99_ms"] / eng["p99_ms"],
+                         "throughput": eng["gkeys_per_s"] / pla["gkeys_per_s"]},
+            "capacity": capacity, "engine_stats": e_stats, "check": check,
+            "gpu_launches": e_launches}
+
+
+def run_serving(args, rank, world, local_rank):
+    """Config: a request stream served by the engine, against one request at a time."""
+    import torch
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if rank != 0:  # one GPU per stream; replicas would serve independent streams
+        return
+    m = measure_serving(args, dev, args.requests, verify=not args.no_verify)
     line = {
-        "metric": SERVE_METRIC, "value": eng["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": nreq, "warmup": n_cal,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": serve_desc(nreq, args.load, args.budget_gb), "rate_per_s": rate,
-                   "plain_service_ms": service * 1e3},
-        "engine": eng, "plain": pla,
-        "vs_plain": {"p50": pla["p50_ms"] / eng["p50_ms"], "p99": pla["p99_ms"] / eng["p99_ms"],
-                     "throughput": eng["gkeys_per_s"] / pla["gkeys_per_s"]},
-        "capacity": capacity,
-        "engine_stats": e_stats,
-        "check": {"sampled_probes": len(sample), "engine_equals_plain": bool(same)},
-        "gpu_launches": int(e_stats["builds"] + e_stats["probe_launches"]),
+        "metric": SERVE_METRIC, "value": m["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": m["requests"],
+        "warmup": m["config"]["calibration_requests"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": m["config"],
     }
+    line.update({k: m[k] for k in ("engine", "plain", "vs_plain", "capacity", "engine_stats", "check",
+                                   "gpu_launches")})
     print(json.dumps(line), flush=True)
+
+
+def measure_plain_small(args, dev):
+    """The 2^20 configuration: 2^20 uniform uint32 keys, B = 2^20, 2^20 queries
+    with 50% hits, build + count per step.  Its 8 MiB of inputs fit in L2, so a
+    256 MiB buffer is written between steps (outside the timed events) and each
+    step is timed alone; the step's counts are checked against the oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2104_00792_gb300 as hg
+    import workloads as W
+
+    n = 1 << 20
+    wl = W.plain_uniform(n, n, num_buckets=n)
+    keys = torch.from_numpy(wl.keys.view(np.int32)).to(dev)
+    queries = torch.from_numpy(wl.queries.view(np.int32)).to(dev)
+    counts = torch.empty(n, dtype=torch.int32, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        t = hg.hg_build(keys, n, 0, stream=stream)
+        hg.hg_query_count(t, queries, counts, total, stream=stream)
+        t.free(stream)
+
+    for _ in range(10):
+        step()
+    steps = 200
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize(dev)
+    launches0 = hg.hg_launch_count()
+    for a, b in evs:
+        flush.fill_(1)
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = (hg.hg_launch_count() - launches0) // steps
+    times = np.array([a.elapsed_time(b) for a, b in evs])
+    ref = oracle.build_table(wl.keys, n, 0)
+    want = ref.query_count(wl.queries)
+    ok = bool(np.array_equal(counts.cpu().numpy().view(np.uint32).astype(np.uint64), want))
+    ok &= int(total.cpu().numpy().view(np.uint64)[0]) == int(want.sum())
+    mean = float(times.mean())
+    return {"value": 2 * n / (mean * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": mean,
+            "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)), "steps": steps,
+            "config": {"workload": "plain_uniform: N=2^20 uint32 keys uniform, B=2^20, murmur3-fmix32 seed 0, "
+                                   "Q=2^20 queries 50% hits; step = hg_build + hg_query_count(counts, total) + hg_free",
+                       "l2": "inputs fit in L2: 256 MiB written between steps, outside each step's events"},
+            "kernel_launches_per_step": launches,
+            "check": {"oracle_counts_and_total_equal": ok}}
+
+
+def measure_join(args, dev, with_oracle=True):
+    """The key-value join configuration: 2^27 (uint64 key, uint32 value) pairs,
+    B = 2^26; a probe relation of 2^26 keys (half hits, a 5% subset repeated 8x).
+    Step = hg_build + hg_join_count (the join's cardinality) + hg_query_gather
+    of the first 2^20 probes (two-call pattern, capacity known) + hg_free."""
+    import numpy as np
+    import torch
+
+    import paper_2104_00792_gb300 as hg
+    import workloads as W
+
+    n, B, q, qg = 1 << 27, 1 << 26, 1 << 26, 1 << 20
+    wl = W.join_kv(n=n, num_buckets=B, q=q)
+    keys = torch.from_numpy(wl.keys.view(np.int64)).to(dev)
+    vals = torch.from_numpy(wl.values.view(np.int32)).to(dev)
+    queries = torch.from_numpy(wl.queries.view(np.int64)).to(dev)
+    first = queries[:qg].contiguous()
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    offs = torch.empty(qg + 1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    with hg.hg_build(keys, B, 0, values=vals, stream=stream) as t:
+        try:
+            hg.hg_query_gather(t, first, offs, None, stream=stream)
+            m = 0
+        except hg.HashGraphError as e:
+            m = e.total
+        walk = hg.hg_probe_stats(t, queries, stream=stream)
+        walk_g = hg.hg_probe_stats(t, first, stream=stream)
+    out_vals = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    state = {}
+
+    def step():
+        t = hg.hg_build(keys, B, 0, values=vals, stream=stream)
+        hg.hg_join_count(t, queries, total, stream=stream)
+        state["m"] = hg.hg_query_gather(t, first, offs, out_vals, stream=stream)
+        t.free(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    steps = max(5, args.steps // 2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = hg.hg_launch_count()
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = (hg.hg_launch_count() - launches0) // steps
+    ms = ev0.elapsed_time(ev1) / steps
+    # per-kernel times from a second run
+    hg.hg_prof_enable(True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    hg.hg_prof_enable(False)
+    prof = {name: hg.hg_prof_read(name) for name in hg.hg_prof_names()}
+    kernels = {name: {"launches": c // 3, "ms_per_launch": tot / c} for name, (c, tot) in prof.items() if c}
+    peak, peak_kind = measured_peak()
+    k, v = 8, 4
+    build_bytes = (3 * k + 2 * v) * n + 16 * B
+    join_bytes = (k + 8) * q + k * walk["walked"]
+    gather_bytes = (k + 8) * qg + k * walk_g["walked"] + 8 * (qg + 1) + 4 * m
+    model = build_bytes + join_bytes + gather_bytes
+    total_got = int(total.cpu().numpy().view(np.uint64)[0])
+    res = {"value": (n + q) / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "config": {"workload": "join_kv: N=2^27 (uint64 key uniform, uint32 value) pairs, B=2^26, murmur3-fmix64 "
+                                  "seed 0; probe relation of 2^26 uint64 keys, 50% hits, a 5% subset repeated 8x; "
+                                  "step = hg_build + hg_join_count + hg_query_gather(first 2^20 probes) + hg_free",
+                      "l2": "inputs exceed L2 (2 GiB read per step); no flush"},
+           "roofline": {"bound": "hbm", "step_model_alg_bytes": model,
+                        "step_model_alg": "(3k+2v)N + 16B + (k+8)Q + kW + gather ((k+8)Qg + kWg + 8(Qg+1) + 4M), "
+                                          "k=8, v=4",
+                        "achieved": model / (ms * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                        "step_frac_alg": model / (ms * 1e-3) / 1e9 / peak},
+           "kernels": kernels, "walk": {"walked": walk["walked"], "walked_first_2^20": walk_g["walked"]},
+           "join_total": total_got, "gathered_values": state["m"],
+           "kernel_launches_per_step": launches}
+    if with_oracle:
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.build_table(wl.keys, B, 0, values=wl.values)
+        want_total = ref.join_count(wl.queries)
+        ro, rv = ref.query_gather(wl.queries[:qg])
+        dt = time.perf_counter() - t0
+        go = offs.cpu().numpy().view(np.uint64)
+        gv = out_vals.cpu().numpy().view(np.uint32)[: state["m"]]
+        seg = np.repeat(np.arange(qg), np.diff(ro.astype(np.int64)))
+        ok_g = bool(np.array_equal(go, ro)) and gv.size == rv.size and bool(
+            np.array_equal(gv[np.lexsort((gv, seg))], rv[np.lexsort((rv, seg))]))
+        res["check"] = {"oracle_join_total_equal": total_got == want_total, "oracle_gather_equal": ok_g}
+        res["cpu_baseline"] = {"value": (n + q) / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"the whole configuration: oracle build of 2^27 pairs + join count of 2^26 "
+                                         f"probes + gather of the first 2^20, {dt:.1f} s on one thread",
+                               "host": host_cpu()}
+    return res
 
 
 DUP_METRIC = "duplicate-key sweep: build and query Gkeys/s vs copies per value"

@@ -240,9 +240,13 @@ hg_status hg_probe_stats(const hg_table* t, const void* d_queries, uint64_t q, u
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  All calls
  * share the array: calls whose GPU work overlaps (other streams or threads)
- * race on it, so order them on one stream.  A kernel that gives up a bounded
- * wait leaves d_offsets[V] != n, which a caller can check after the stream
- * syncs.  Asynchronous, like hg_build.
+ * race on it, so order them on one stream.  Device-side errors are not
+ * returned as a status (there is no table to hold an error word): a kernel
+ * that gives up a bounded wait leaves d_offsets[V] != n, so a caller checks
+ * d_offsets[V] == n after the stream syncs.  The looked-up address is kept for
+ * the life of the process, which assumes the device's primary context is not
+ * reset (cudaDeviceReset) while the library is loaded.  Asynchronous, like
+ * hg_build.
  */
 hg_status hg_build_noalloc(const hg_config* cfg, const void* d_keys, const void* d_values, uint64_t n,
                            uint32_t* d_offsets, void* d_keys_out, uint32_t* d_values_out, hg_stream_t s);

@@ -11,8 +11,11 @@
 // Every GPU that loads the library holds it until the process exits.  Host
 // code cannot use the array's name as a device address (on the host it names
 // a host-side stand-in), so the first call on each device looks up the real
-// address with cudaGetSymbolAddress, with that device current, and caches it.
-// That first call should therefore happen before any stream capture.
+// address with cudaGetSymbolAddress, with that device current, and caches it
+// for the life of the process (so the device's primary context must not be
+// reset while the library is loaded).  That first call should therefore happen
+// before any stream capture.  Device-side errors are not returned as a status:
+// a build whose prefix sum gave up a bounded wait leaves d_offsets[V] != n.
 //
 // All calls share the one array and it keeps the last call's contents: each
 // call clears the parts that must start at zero.  Calls whose work overlaps

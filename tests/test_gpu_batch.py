@@ -98,6 +98,21 @@ def test_batch_edge_tables(hg):
     _check(wl, got, tabs, seed=0x1234)
 
 
+def test_batch_largest_tables(hg):
+    # the top of the batched workload's size range: tables of 2^19 to 2^20 keys
+    # with B_t = N_t (128 bins of 8192 buckets each, partitioned inside one CTA),
+    # mixed with small tables on the fused shared-memory path
+    big = W.batched_uniform(6, 19, 20, salt=31)
+    small = W.batched_uniform(10, 8, 13, salt=32)
+    tables = [big.table(t) for t in range(big.n_tables)] + [small.table(t) for t in range(small.n_tables)]
+    wl = _concat([(np.ascontiguousarray(k), B, np.ascontiguousarray(q)) for k, B, q in tables])
+    assert max(int(x) for x in wl.num_buckets) >= 1 << 19
+    got, tabs, _ = _run(hg, wl)
+    _check(wl, got, tabs)
+    got2, tabs2, _ = _run(hg, wl, tune=True)
+    _check(wl, got2, tabs2)
+
+
 @pytest.mark.parametrize("params", PARAMS)
 def test_batch_every_parameter_set(hg, params):
     wl = W.batched_uniform(24, 6, 15, salt=9)

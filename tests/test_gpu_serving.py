@@ -82,6 +82,27 @@ def test_serving_counts_equal_the_oracle(hg, max_batch, poll_p):
         assert np.array_equal(got, refs[t].query_count(q)), f"probe {rid} on table {t}"
 
 
+def test_serving_at_configured_sizes(hg):
+    # builds of up to 2^20 keys and probes of up to 2^18 queries (the top of the
+    # range is the serving workload's own shape), budget forcing evictions; every
+    # probe's counts against the oracle on its table alone
+    budget = 24 * 10**6
+    trace = W.serving_trace(160, build_log2=(10, 20), probe_log2=(8, 18), budget_bytes=budget, salt=23)
+    assert max(r.size for r in trace if r.kind == "build") > 1 << 18
+    assert max(r.size for r in trace if r.kind == "probe") > 1 << 16
+    keys_of, probes, done, stats = _serve(hg, trace, budget, 64, 0.25, seed=23)
+    assert stats["evictions"] > 0, "the budget should have forced evictions"
+    assert all(st == hg.HG_OK for st in done.values())
+    assert len(done) == len(trace)
+    n_of = W.serve_table_n(trace)
+    refs = {}
+    for rid, t, q, _, counts in probes:
+        if t not in refs:
+            refs[t] = oracle.build_table(keys_of[t][0], n_of[t], 0)
+        got = from_dev(counts, np.uint32)[: q.size].astype(np.uint64)
+        assert np.array_equal(got, refs[t].query_count(q)), f"probe {rid} on table {t}"
+
+
 def test_serving_refuses_evicted_and_oversized(hg):
     budget = hg.hg_server_table_bytes(1000, 1000) * 2
     with hg.Server(budget) as srv:

@@ -28,8 +28,9 @@ def hg():
     return m
 
 
-def _noalloc(hg, keys_dev, n, B, seed, values_dev=None, flags=0, key_bytes=4):
-    offs = torch.empty(B + 1, dtype=torch.int32, device="cuda")
+def _noalloc(hg, keys_dev, n, B, seed, values_dev=None, flags=0, key_bytes=4, offs_shift=0):
+    # offs_shift: place d_offsets that many 4-byte words into a larger buffer (unaligned to 16 bytes)
+    offs = torch.empty(B + 1 + offs_shift, dtype=torch.int32, device="cuda")[offs_shift:]
     kout = torch.empty(max(n, 1), dtype=keys_dev.dtype, device="cuda")
     has_vals = values_dev is not None or bool(flags & hg.HG_INDEX_VALUES)
     vout = torch.empty(max(n, 1), dtype=torch.int32, device="cuda") if has_vals else None
@@ -43,11 +44,19 @@ def _noalloc(hg, keys_dev, n, B, seed, values_dev=None, flags=0, key_bytes=4):
     return offs, kout[:n], (vout[:n] if vout is not None else None)
 
 
-def _same_as_hg_build(hg, keys, B, seed, values=None, flags=0):
+def _same_as_hg_build(hg, keys, B, seed, values=None, flags=0, offs_shift=0, no_device_alloc=False):
     dt = keys.dtype
     dk = to_dev(keys)
     dv = None if values is None else to_dev(values)
-    offs, kout, vout = _noalloc(hg, dk, keys.size, B, seed, dv, flags, keys.dtype.itemsize)
+    torch.cuda.synchronize()
+    if no_device_alloc:
+        # every device allocation the library might make fails from here on
+        hg.hg_debug_fail_alloc_after(0)
+    try:
+        offs, kout, vout = _noalloc(hg, dk, keys.size, B, seed, dv, flags, keys.dtype.itemsize, offs_shift)
+    finally:
+        hg.hg_debug_fail_alloc_after(-1)
+    assert int(from_dev(offs[-1:], np.uint32)[0]) == keys.size  # the build completed
     with hg.hg_build(dk, B, seed, values=dv, flags=flags) as t:
         o_ref, k_ref, v_ref = table_arrays(hg, t, dt)
     o = from_dev(offs, np.uint32)
@@ -80,3 +89,21 @@ def test_noalloc_largest_table_and_rejection(hg):
     st = hg.lib.hg_build_noalloc(ctypes.byref(cfg), None, None, 0, offs.data_ptr(), None, None, None)
     assert st == hg.HG_ERR_INVALID_ARG
     assert b"num_buckets" in hg.lib.hg_last_error()
+
+
+def test_noalloc_makes_no_device_allocation(hg):
+    # with every library allocation made to fail, the build still succeeds: it
+    # allocates nothing (checked twice in a row on different shapes)
+    wl = W.plain_uniform(200_003, 16, num_buckets=(1 << 18) + 3)
+    _same_as_hg_build(hg, wl.keys, (1 << 18) + 3, 5, flags=hg.HG_INDEX_VALUES, no_device_alloc=True)
+    wl2 = W.join_kv(n=30001, num_buckets=4099, q=16, salt=4)
+    _same_as_hg_build(hg, wl2.keys, 4099, 0, values=wl2.values, no_device_alloc=True)
+
+
+def test_noalloc_unaligned_offsets_at_the_largest_table(hg):
+    # offsets 4 bytes past a 16-byte boundary take the prefix sum's scalar path,
+    # which uses the most tiles (and so the most of the fixed array) at the limit
+    B = (1 << 23) - 1
+    wl = W.plain_uniform((1 << 20) + 17, 16, num_buckets=B, salt=6)
+    _same_as_hg_build(hg, wl.keys, B, 0, offs_shift=1)
+    _same_as_hg_build(hg, wl.keys, B, 0, offs_shift=3)
