@@ -534,9 +534,11 @@ def run_ours(args, rank, world, local_rank):
         "part_hist": k * N,                           # bin histogram + first-pass chunk counts
         "chunk_count": k * N,                         # second-pass chunk counts
         "part_scatter": 2 * k * N,                    # one partition pass
+        "part_scatter2": 2 * k * N,                   # the second (per coarse segment)
         "bin_build": 2 * k * N + o * (B + 1),         # per-bin counting sort: keys in, keys + offsets out
         "q_part_count": k * Q,
         "q_partition": 2 * k * Q + 4 * Q,             # queries grouped + their positions
+        "q_partition2": 2 * k * Q + 4 * Q,
         "probe": k * Q + 8 * Q + k * (W - WL) + 4 * Q,   # direct probe (tables that stay in L2)
         "long": k * WL,
     }

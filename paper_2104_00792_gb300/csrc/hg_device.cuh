@@ -20,6 +20,20 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     return h;
 }
 
+// Inverse of fmix32 (a bijection of 32-bit words): its steps undone in reverse
+// order.  x ^= x >> 16 is its own inverse; x ^= x >> 13 is undone by
+// x ^= (x >> 13) ^ (x >> 26); a product with an odd constant by the product
+// with the constant's inverse mod 2^32 (0x85ebca6b * 0xa5cb9243 = 1 and
+// 0xc2b2ae35 * 0x7ed1b41d = 1 mod 2^32).
+__device__ __forceinline__ uint32_t fmix32_inv(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x7ed1b41du;
+    h ^= (h >> 13) ^ (h >> 26);
+    h *= 0xa5cb9243u;
+    h ^= h >> 16;
+    return h;
+}
+
 // MurmurHash3 64-bit finaliser.
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
     k ^= k >> 33;
@@ -41,6 +55,16 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t k, const Hasher& H) {
     if (H.mode == MODE_POW2) return (uint32_t)(h & H.mask);
     return (uint32_t)(h % H.B);
 }
+
+// The build's and the query grouping's intermediate arrays of 32-bit keys hold
+// each key's hash h = fmix32(k ^ seed) instead of the key, so that later passes
+// need no hashing; the key comes back as fmix32_inv(h) ^ seed.
+__device__ __forceinline__ uint32_t bucket_of_hash(uint32_t h, const Hasher& H) {
+    if (H.mode == MODE_POW2) return h & (uint32_t)H.mask;
+    return (uint32_t)__umul64hi(H.magic * (uint64_t)h, H.B);
+}
+__device__ __forceinline__ uint32_t hash_key32(uint32_t k, const Hasher& H) { return fmix32(k ^ (uint32_t)H.seed); }
+__device__ __forceinline__ uint32_t unhash_key32(uint32_t h, const Hasher& H) { return fmix32_inv(h) ^ (uint32_t)H.seed; }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }

@@ -106,7 +106,8 @@ cudaError_t summary_prepare(Table& t, cudaStream_t s);
 cudaError_t summary_finish(Table& t, cudaStream_t s);
 
 // Queries grouped by the table's bins (ranges of 8192 buckets), so that a
-// bin's offsets and keys stay in L1 while its queries are probed; the counts,
+// bin's offsets and keys stay in L1 while its queries are probed (32-bit
+// queries are grouped as their hashes, items.qunhash saying so); the counts,
 // produced in grouped order, go back to slot order through reverse passes.
 // Chunk c of a partition pass: keys [lo, hi) of segment `seg` (see chunk_range).
 struct ChunkMap {
@@ -127,6 +128,9 @@ struct BinWork {
     const uint32_t* huge_chunk_start = nullptr;
     const uint32_t* work = nullptr;
     uint32_t huge_chunk = 0;
+    // 32-bit grouped queries are held as their hashes (see group_queries): then
+    // (1 << 32 | seed), and a probe recovers each query as fmix32_inv(h) ^ seed
+    uint64_t qunhash = 0;
 };
 struct GroupedQueries {
     void* mem = nullptr;

@@ -151,6 +151,7 @@ struct Plan {
     uint32_t n_huge;       // bins split over many CTAs (at most MAX_HUGE)
     uint32_t huge_chunks;  // their HUGE_CHUNK-key work items
     uint32_t n_work;       // bins handled whole by one CTA
+    uint32_t n_big;        // the first n_big of them hold more than the plan's big_t keys
 };
 
 // Chunk c of a pass: keys [lo, hi) of segment `seg`.  Single-segment passes
@@ -214,7 +215,7 @@ k_part_count(const K* __restrict__ keys, uint64_t n, Hasher H, uint32_t P, uint3
 }
 
 // Second-pass chunk counts: digit = bin & (RADIX - 1) inside each chunk's segment.
-template <typename K>
+template <typename K, bool HIN = false>
 __global__ void __launch_bounds__(PASS_THREADS)
 k_chunk_count(const K* __restrict__ in, Hasher H, ChunkMap cm, const Plan* __restrict__ plan, uint32_t* chunk_cnt) {
     __shared__ uint32_t s_dig[RADIX];
@@ -226,7 +227,8 @@ k_chunk_count(const K* __restrict__ in, Hasher H, ChunkMap cm, const Plan* __res
     for (uint32_t i = threadIdx.x; i < RADIX; i += blockDim.x) s_dig[i] = 0;
     __syncthreads();
     block_for_range<K, false, 4>(in, nullptr, lo, hi, [&](uint64_t, K k, uint32_t, unsigned) {
-        atomicAdd(s_dig + (bin_of(k, H) & (RADIX - 1)), 1u);
+        const uint32_t bin = HIN ? bucket_of_hash((uint32_t)k, H) >> BIN_SHIFT : bin_of(k, H);
+        atomicAdd(s_dig + (bin & (RADIX - 1)), 1u);
     });
     __syncthreads();
     for (uint32_t d = threadIdx.x; d < RADIX; d += blockDim.x) chunk_cnt[(uint64_t)c * RADIX + d] = s_dig[d];
@@ -339,6 +341,7 @@ k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uin
         plan->n_huge = n_huge;
         plan->huge_chunks = cr;
         plan->n_work = nbig + nsmall;
+        plan->n_big = nbig;
     }
 }
 
@@ -538,6 +541,197 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
     }
 }
 
+// ------------------------------------------------- downsweep, 32-bit keys --
+// k_pass_down for 32-bit keys, with each key's hash as the word that moves:
+// the pass reads keys (HIN = false, hashing each once) or hashes (HIN = true)
+// and always writes hashes, so the next pass, the bin build and the grouped
+// probes take a key's bucket straight from its word (the key itself is
+// fmix32_inv(h) ^ seed).  Because of that the staging keeps only the words:
+// the write-out recomputes each staged word's digit (a mask and a shift) to
+// find its run's destination, instead of staging a destination per word,
+// which halves the shared-memory traffic of the scatter.  A tile is 256
+// threads x IPT words (8192 without payloads; 4096 with): few threads with
+// many words each, so the tile's four barriers and its digit scan are
+// amortised over more keys.  Element li of a tile is held by thread
+// (li / 4) % 256, slot (li / 1024) * 4 + li % 4.
+constexpr int P32_THREADS = 256;
+template <int PM>
+struct P32 {
+    static constexpr int IPT = PM ? 16 : 32;
+    static constexpr int TILE = P32_THREADS * IPT;
+};
+static_assert(CHUNK + 3 <= TILES_PER_CHUNK * (uint32_t)P32<0>::TILE && CHUNK + 3 <= TILES_PER_CHUNK * (uint32_t)P32<1>::TILE,
+              "a chunk's window (the chunk and up to 3 words before it) spans at most TILES_PER_CHUNK tiles");
+
+template <bool HIN, int PM, bool DR, bool POW2>
+__global__ void __launch_bounds__(P32_THREADS, 2)
+k_pass32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_t n, Hasher H,
+         uint32_t dig_shift, uint32_t dig_mask, uint32_t R, ChunkMap cm, uint32_t nch_host,
+         const Plan* __restrict__ plan, const uint32_t* __restrict__ chunk_base, uint32_t* __restrict__ out,
+         uint32_t* __restrict__ out_v, uint32_t* err, uint32_t* __restrict__ dr_out, uint2* __restrict__ tile_lb,
+         uint32_t in_padded) {
+    constexpr int IPT = P32<PM>::IPT;
+    constexpr int TILE = P32<PM>::TILE;
+    constexpr int NG = IPT / 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);  // staged words [TILE]
+    uint32_t* s_pay = s_h + TILE;                       // staged payloads [TILE] (PM)
+    __shared__ uint32_t s_cnt[RADIX], s_run[RADIX], s_warp[4];
+    __shared__ uint2 s_lb[RADIX];  // (offset of the digit's run inside the tile, its destination)
+    const uint32_t tid = threadIdx.x;
+    const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
+    const uint32_t c = blockIdx.x;
+    if (c >= nch) return;
+    uint32_t seg, first;
+    uint64_t lo64, hi64;
+    chunk_range(cm, c, seg, first, lo64, hi64);
+    // Tiles cover the chunk's window, which starts at the 16-byte boundary at or
+    // before the chunk: window position x is element lo - a + x, valid for
+    // a <= x < end, so every 4-word group is one aligned 16-byte load (the few
+    // words around the chunk are read and ignored; in_padded: the input may be
+    // read up to 3 words past its end, else the last group is read word by word)
+    const uint32_t a = (uint32_t)(lo64 & 3);
+    const uint32_t end = a + (uint32_t)(hi64 - lo64);
+    const uint32_t* __restrict__ inc = in + (lo64 - a);
+    const uint32_t* __restrict__ inc_v = PM == 1 ? in_v + (lo64 - a) : nullptr;
+    uint32_t* __restrict__ drc = DR ? dr_out + (lo64 - a) : nullptr;
+    uint2* __restrict__ lbc = DR ? tile_lb + (uint64_t)c * TILES_PER_CHUNK * RADIX : nullptr;
+    const uint32_t base32 = (uint32_t)(lo64 - a);  // (index payloads: positions fit 32 bits)
+    const bool vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0 &&
+                     (PM != 1 || (reinterpret_cast<uintptr_t>(in_v) & 15) == 0);
+    const uint32_t vend = in_padded ? end + 3 : end;  // groups wholly below vend are read as vectors
+    const bool dr_vec = DR && (reinterpret_cast<uintptr_t>(dr_out) & 15) == 0;
+    for (uint32_t d = tid; d < RADIX; d += P32_THREADS) {
+        s_cnt[d] = 0;
+        s_run[d] = d < R ? chunk_base[(uint64_t)c * RADIX + d] : 0u;
+    }
+    // the digit is masked to the radix, so shared-memory indices stay in bounds
+    // whatever the word; a consistent plan never needs the mask.  POW2: B = 2^k,
+    // the bucket is the hash's low k bits
+    const uint32_t bmask = (uint32_t)H.mask, dsh = BIN_SHIFT + dig_shift, dmask = dig_mask & (RADIX - 1);
+    auto digit = [&](uint32_t h) {
+        if (POW2) return ((h & bmask) >> dsh) & dmask;
+        return (bucket_of_hash(h, H) >> dsh) & dmask;
+    };
+    uint32_t w[IPT];
+    uint32_t v[PM ? IPT : 1];
+    // element li of a tile: thread (li / 4) % 256, slot (li / 1024) * 4 + li % 4
+    auto load = [&](uint32_t t0, bool full) {
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const uint32_t x0 = t0 + (tid + g * P32_THREADS) * 4;
+            if (full || (vec && x0 + 4 <= vend)) {
+                const uint4 q = ld_stream16(inc + x0);
+                w[4 * g] = q.x;
+                w[4 * g + 1] = q.y;
+                w[4 * g + 2] = q.z;
+                w[4 * g + 3] = q.w;
+                if (PM == 1) {
+                    const uint4 y = ld_stream16(inc_v + x0);
+                    v[4 * g] = y.x;
+                    v[4 * g + 1] = y.y;
+                    v[4 * g + 2] = y.z;
+                    v[4 * g + 3] = y.w;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = x0 + u >= a && x0 + u < end;
+                    w[4 * g + u] = ok ? inc[x0 + u] : 0u;
+                    if (PM == 1) v[4 * g + u] = ok ? inc_v[x0 + u] : 0u;
+                }
+            }
+            if (PM == 2) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[4 * g + u] = base32 + x0 + u;
+            }
+        }
+    };
+    auto is_full = [&](uint32_t t0) { return vec && t0 >= a && t0 + (uint32_t)TILE <= end; };
+    const uint32_t nn = (uint32_t)min(n, (uint64_t)0xffffffffu);
+    uint32_t bad = 0;
+    // one tile; FULL: all TILE words valid and loaded with 16-byte loads (no per-word checks)
+    auto tile = [&](uint32_t t0, auto full_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        const uint32_t cnt_tile = FULL ? (uint32_t)TILE : min(end, t0 + (uint32_t)TILE) - max(a, t0);
+        uint32_t dr[IPT];  // rank << 8 | digit (all ones: no word)
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            if (!HIN) w[j] = hash_key32(w[j], H);
+            const uint32_t d = digit(w[j]);
+            const uint32_t x = t0 + (tid + (j / 4) * P32_THREADS) * 4 + (j % 4);
+            const bool ok = FULL || (x >= a && x < end);
+            dr[j] = ok ? ((atomicAdd(s_cnt + d, 1u) << 8) | d) : 0xffffffffu;
+        }
+        __syncthreads();
+        // digit offsets inside the tile (first 4 warps), and where each run goes
+        if (tid < RADIX) {
+            const uint32_t d = tid;
+            const uint32_t cd = s_cnt[d];
+            const uint32_t incl = warp_inclusive_scan(cd);
+            if (lane_id() == 31) s_warp[d >> 5] = incl;
+            asm volatile("bar.sync 1, 128;");
+            uint32_t wp = 0;
+            for (uint32_t x = 0; x < (d >> 5); ++x) wp += s_warp[x];
+            const uint2 lb = make_uint2(wp + incl - cd, s_run[d]);
+            s_lb[d] = lb;
+            if (DR) lbc[(t0 / TILE) * RADIX + d] = lb;
+            s_run[d] += cd;
+            s_cnt[d] = 0;
+        }
+        __syncthreads();
+        if (DR) {
+            if (FULL && dr_vec) {
+#pragma unroll
+                for (int g = 0; g < NG; ++g)
+                    *reinterpret_cast<uint4*>(drc + t0 + (tid + g * P32_THREADS) * 4) =
+                        make_uint4(dr[4 * g], dr[4 * g + 1], dr[4 * g + 2], dr[4 * g + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < IPT; ++j)
+                    if (dr[j] != 0xffffffffu) drc[t0 + (tid + (j / 4) * P32_THREADS) * 4 + (j % 4)] = dr[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            if (FULL || dr[j] != 0xffffffffu) {
+                const uint32_t pos = s_lb[dr[j] & 0xffu].x + (dr[j] >> 8);
+                s_h[pos] = w[j];
+                if (PM) s_pay[pos] = v[j];
+            }
+        }
+        __syncthreads();
+        // prefetch the next tile while this one is written out
+        const uint32_t t1 = t0 + TILE;
+        if (t1 < end) load(t1, is_full(t1));
+        auto put = [&](uint32_t i) {
+            const uint32_t h = s_h[i];
+            const uint2 lb = s_lb[digit(h)];
+            const uint32_t dst = lb.y + (i - lb.x);
+            if (dst < nn) {
+                out[dst] = h;
+                if (PM) out_v[dst] = s_pay[i];
+            } else {
+                bad = 1;
+            }
+        };
+        if (FULL) {
+#pragma unroll 8
+            for (int r = 0; r < IPT; ++r) put(tid + r * P32_THREADS);
+        } else {
+            for (uint32_t i = tid; i < cnt_tile; i += P32_THREADS) put(i);
+        }
+        __syncthreads();
+    };
+    __syncthreads();
+    if (end > a) load(0, is_full(0));
+    for (uint32_t t0 = 0; t0 < end; t0 += TILE) {
+        if (is_full(t0)) tile(t0, std::true_type{});
+        else tile(t0, std::false_type{});
+    }
+    if (bad) atomicOr(err, DEVERR_BOUNDS);
+}
+
 // ---------------------------------------------------------------- reverse --
 // Undo one DR-recording pass for 32-bit values: src is in the pass's output
 // order, dst receives the values in its input order.  Each tile reads the runs
@@ -547,11 +741,12 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
 // copies into shared memory, all of a thread's in flight at once, and the next
 // tile's records are requested while they land.
 template <typename K>
-__global__ void __launch_bounds__(PASS_THREADS, 3)
+__global__ void __launch_bounds__(PASS_THREADS, sizeof(K) == 4 ? 2 : 3)
 k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, ChunkMap cm, uint32_t nch_host,
                const Plan* __restrict__ plan, const uint32_t* __restrict__ dr_in, const uint2* __restrict__ tile_lb,
                uint32_t* err) {
-    constexpr int TILE = PassCfg<K>::TILE;
+    // the forward pass's tile: k_pass32 for 32-bit keys, k_pass_down otherwise
+    constexpr int TILE = sizeof(K) == 4 ? P32<0>::TILE : PassCfg<K>::TILE;
     constexpr int PER = TILE / PASS_THREADS;
     __shared__ uint32_t s_val[TILE];
     __shared__ uint8_t s_dig[TILE];
@@ -562,21 +757,27 @@ k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, Chu
     uint32_t seg, first;
     uint64_t lo, hi;
     chunk_range(cm, c, seg, first, lo, hi);
+    // tiles as the forward pass cut them: for 32-bit keys from the 16-byte
+    // boundary at or before the chunk's start (window position x = element
+    // lo - a + x, valid for a <= x < end), for 64-bit keys from the start
+    const uint32_t a = sizeof(K) == 4 ? (uint32_t)(lo & 3) : 0u;
+    const uint32_t end = a + (uint32_t)(hi - lo);
+    const uint32_t* __restrict__ drc = dr_in + (lo - a);
+    uint32_t* __restrict__ dstc = dst + (lo - a);
     uint32_t drs[PER];
     uint2 lbr = make_uint2(0, 0);
-    auto fetch = [&](uint64_t t0) {
-        const uint32_t cnt = (uint32_t)min((uint64_t)TILE, hi - t0);
+    auto fetch = [&](uint32_t t0) {
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
-            const uint32_t li = threadIdx.x + j * PASS_THREADS;
-            drs[j] = li < cnt ? __ldg(dr_in + t0 + li) : 0xffffffffu;
+            const uint32_t x = t0 + threadIdx.x + j * PASS_THREADS;
+            drs[j] = (x >= a && x < end) ? __ldg(drc + x) : 0xffffffffu;
         }
         if (threadIdx.x < RADIX)
-            lbr = __ldg(tile_lb + ((uint64_t)c * TILES_PER_CHUNK + (t0 - lo) / TILE) * RADIX + threadIdx.x);
+            lbr = __ldg(tile_lb + ((uint64_t)c * TILES_PER_CHUNK + t0 / TILE) * RADIX + threadIdx.x);
     };
-    if (lo < hi) fetch(lo);
-    for (uint64_t t0 = lo; t0 < hi; t0 += TILE) {
-        const uint32_t cnt_tile = (uint32_t)min((uint64_t)TILE, hi - t0);
+    if (end > a) fetch(0);
+    for (uint32_t t0 = 0; t0 < end; t0 += TILE) {
+        const uint32_t cnt_tile = min(end, t0 + (uint32_t)TILE) - max(a, t0);  // valid elements
         if (threadIdx.x < RADIX) s_lb[threadIdx.x] = lbr;
         __syncthreads();
         // every element marks its staging position with its digit ...
@@ -608,17 +809,17 @@ k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, Chu
                 cp_async4(s_val + i, src + lb.y + (i - lb.x));
             }
         }
-        const uint64_t t1 = t0 + TILE;
-        if (t1 < hi) fetch(t1);
+        const uint32_t t1 = t0 + TILE;
+        if (t1 < end) fetch(t1);
         cp_async_wait_all();
         __syncthreads();
         // s_lb and s_dig are not read past this point, and s_val is next written
         // after the next tile's second barrier, so no barrier ends the tile
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
-            const uint32_t li = threadIdx.x + j * PASS_THREADS;
+            const uint32_t x = t0 + threadIdx.x + j * PASS_THREADS;
             const uint32_t pos = (pj[j / 2] >> ((j & 1) * 16)) & 0xffffu;
-            if (pos != 0xffffu) dst[t0 + li] = s_val[pos];
+            if (pos != 0xffffu) dstc[x] = s_val[pos];
         }
     }
 }
@@ -641,7 +842,19 @@ __device__ __forceinline__ void huge_item(uint32_t item, uint32_t n_huge, const 
 }
 
 // Huge bins, step 1: per-chunk bucket histograms added into huge_count[e][*].
-template <typename K>
+// HIN: the keys are 32-bit hashes (the partition passes' words), the bucket is taken from them.
+template <typename K, bool HIN>
+__device__ __forceinline__ uint32_t bucket_in(K k, const Hasher& H) {
+    if constexpr (HIN) return bucket_of_hash((uint32_t)k, H);
+    else return bucket_of(k, H);
+}
+template <typename K, bool HIN>
+__device__ __forceinline__ K key_in(K k, const Hasher& H) {
+    if constexpr (HIN) return (K)unhash_key32((uint32_t)k, H);
+    else return k;
+}
+
+template <typename K, bool HIN>
 __global__ void __launch_bounds__(LOCAL_THREADS)
 k_huge_count(const K* __restrict__ in, Hasher H, const uint32_t* __restrict__ bin_start,
              const uint32_t* __restrict__ huge_bin, const uint32_t* __restrict__ huge_chunk_start,
@@ -658,7 +871,7 @@ k_huge_count(const K* __restrict__ in, Hasher H, const uint32_t* __restrict__ bi
         for (uint32_t j = threadIdx.x; j < BPB; j += blockDim.x) s_cnt[j] = 0;
         __syncthreads();
         block_for_range<K, false>(in, nullptr, c0, c1, [&](uint64_t, K k, uint32_t, unsigned m) {
-            uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+            uint32_t j = (uint32_t)(bucket_in<K, HIN>(k, H) - b0);
             if (j >= nb) {
                 atomicOr(err, DEVERR_BOUNDS);
                 j = nb - 1;
@@ -701,13 +914,13 @@ k_huge_scan(const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__
 // Step 3 (all bins): work items [0, huge_chunks) place one chunk of a huge bin
 // through its cursors; the following n_work items each take a whole bin.
 // Shared memory: cnt[BPB] | hotmask[BPB/32] | hot list (pos, prefix length) | stage keys | stage payload.
-template <typename K, bool HV>
+template <typename K, bool HV, bool HIN>
 __global__ void __launch_bounds__(LOCAL_THREADS, 2)
 k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_t n, Hasher H,
             const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ work,
             const uint32_t* __restrict__ huge_bin, const uint32_t* __restrict__ huge_chunk_start,
             const Plan* __restrict__ plan, uint32_t* huge_cursor, uint32_t* work_ctr, uint32_t* offsets,
-            K* __restrict__ out, uint32_t* __restrict__ out_v, uint32_t* err, LongFinder LF) {
+            K* __restrict__ out, uint32_t* __restrict__ out_v, uint32_t* err, LongFinder LF, bool big_only) {
     constexpr uint32_t STAGE_CAP = (uint32_t)(LOCAL_STAGE_BYTES / (sizeof(K) + (HV ? 4 : 0)));
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
@@ -722,7 +935,8 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
     const int w = threadIdx.x >> 5;
     constexpr int NW = LOCAL_THREADS / 32;
     const uint64_t B = H.B;
-    const uint32_t n_huge = plan->n_huge, huge_chunks = plan->huge_chunks, n_work = plan->n_work;
+    const uint32_t n_huge = plan->n_huge, huge_chunks = plan->huge_chunks;
+    const uint32_t n_work = big_only ? plan->n_big : plan->n_work;  // big_only: k_bin_small takes the rest
     // candidate thresholds: a bucket with at least THR[k] keys bypasses the staging buffer
     const uint32_t THR[NTHR] = {0xffffffffu, 4096u, 1024u, 256u, 64u};
 
@@ -742,7 +956,7 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             for (uint32_t j = threadIdx.x; j < BPB; j += blockDim.x) s_cnt[j] = 0;
             __syncthreads();
             block_for_range<K, false>(in, nullptr, c0, c1, [&](uint64_t, K k, uint32_t, unsigned m) {
-                uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+                uint32_t j = (uint32_t)(bucket_in<K, HIN>(k, H) - b0);
                 if (j >= nb) j = nb - 1;  // flagged by k_huge_count
                 smem_add1(s_cnt, j, m);
             });
@@ -753,11 +967,11 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             }
             __syncthreads();
             block_for_range<K, HV>(in, in_v, c0, c1, [&](uint64_t, K k, uint32_t v, unsigned m) {
-                uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+                uint32_t j = (uint32_t)(bucket_in<K, HIN>(k, H) - b0);
                 if (j >= nb) j = nb - 1;
                 const uint32_t pos = smem_inc(s_cnt, j, m);
                 if (pos < n) {
-                    out[pos] = k;
+                    out[pos] = key_in<K, HIN>(k, H);
                     if (HV) out_v[pos] = v;
                 } else {
                     atomicOr(err, DEVERR_BOUNDS);
@@ -785,7 +999,7 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
         auto hist = [&](auto fast) {
             // (the placement pass reads these keys again: keep them in L2)
             block_for_range<K, false, 2, true>(in, nullptr, s0, s1, [&](uint64_t, K k, uint32_t, unsigned m) {
-                uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+                uint32_t j = (uint32_t)(bucket_in<K, HIN>(k, H) - b0);
                 if (j >= nb) {
                     atomicOr(err, DEVERR_BOUNDS);
                     j = nb - 1;
@@ -933,11 +1147,11 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
         if (staged && nhot == 0 && !heavy) {
             // the common bin: every key is staged, counters are rarely shared
             block_for_range<K, HV>(in, in_v, s0, s1, [&](uint64_t, K k, uint32_t v, unsigned) {
-                uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+                uint32_t j = (uint32_t)(bucket_in<K, HIN>(k, H) - b0);
                 if (j >= nb) j = nb - 1;  // flagged in pass 1
                 const uint32_t pos = atomicAdd(s_cnt + j, 1u);
                 if (pos < STAGE_CAP) {
-                    s_keys[pos] = k;
+                    s_keys[pos] = key_in<K, HIN>(k, H);
                     if (HV) s_pay[pos] = v;
                 } else {
                     atomicOr(err, DEVERR_BOUNDS);
@@ -945,19 +1159,19 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             });
         } else {
             block_for_range<K, HV>(in, in_v, s0, s1, [&](uint64_t, K k, uint32_t v, unsigned m) {
-                uint32_t j = (uint32_t)(bucket_of(k, H) - b0);
+                uint32_t j = (uint32_t)(bucket_in<K, HIN>(k, H) - b0);
                 if (j >= nb) j = nb - 1;  // flagged in pass 1
                 const uint32_t pos = smem_inc(s_cnt, j, m);
                 const bool hot = !staged || ((s_hot[j >> 5] >> (j & 31)) & 1u);
                 if (!hot) {
                     if (pos < STAGE_CAP) {
-                        s_keys[pos] = k;
+                        s_keys[pos] = key_in<K, HIN>(k, H);
                         if (HV) s_pay[pos] = v;
                     } else {
                         atomicOr(err, DEVERR_BOUNDS);
                     }
                 } else if (pos < n) {
-                    out[pos] = k;
+                    out[pos] = key_in<K, HIN>(k, H);
                     if (HV) out_v[pos] = v;
                 } else {
                     atomicOr(err, DEVERR_BOUNDS);
@@ -985,6 +1199,231 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
     }
 }
 
+// Bins of at most SB_CAP 32-bit keys (no values), one at a time per CTA, read
+// as the partition passes leave them (each key's hash; the keys written out
+// are recovered with fmix32_inv): the bin's words arrive in shared memory by
+// one bulk copy (TMA) issued while the
+// CTA works on the bin before, so no phase waits on HBM.  Each thread holds up
+// to SB_KPT keys in registers with their buckets; the counting sort of
+// Algorithm 1 runs in shared memory (histogram -> exclusive scan, which gives
+// the bin's offsets -> placement back into the same buffer, the keys being in
+// registers by then), and the sorted bin leaves in 16-byte stores.
+constexpr int SB_THREADS = 1024;
+constexpr int SB_KPT = 20;
+constexpr uint32_t SB_CAP = (uint32_t)SB_THREADS * SB_KPT;
+constexpr uint32_t SB_BUF_KEYS = SB_CAP + 8;        // room for the copy's 16-byte alignment at both ends
+constexpr uint32_t SB_WAIT_LIMIT = 1u << 24;        // polls of a copy's barrier before the CTA gives up
+constexpr size_t SB_SMEM = (size_t)BPB * 4 + 2 * (size_t)SB_BUF_KEYS * 4;
+static_assert(BPB == 8 * SB_THREADS, "each thread scans eight buckets");
+
+template <bool POW2, bool LONGS>
+__global__ void __launch_bounds__(SB_THREADS, 1)
+k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restrict__ bin_start,
+            const uint32_t* __restrict__ work, const Plan* __restrict__ plan, uint32_t* __restrict__ offsets,
+            uint32_t* __restrict__ out, uint32_t* err, LongFinder LF) {
+    constexpr int GR = SB_KPT / 4;  // 16-byte groups of keys per thread
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* const s_buf0 = s_cnt + BPB;  // buffer b at s_buf0 + b * SB_BUF_KEYS
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_bin[2], s_lo[2], s_hi[2], s_wsum[SB_THREADS / 32];
+    const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+    const uint32_t n_big = plan->n_big, n_small = plan->n_work - n_big;
+    const uint32_t G = gridDim.x;
+
+    // Static schedule: this CTA takes small bins blockIdx.x, blockIdx.x + G, ...
+    // (they are of similar size).  Thread 0 starts the copy of bin (p, s0, s1)
+    // into buffer b; the bin's number and range are read one bin ahead, so no
+    // phase waits on them.
+    auto start_copy = [&](int b, uint32_t p, uint32_t s0, uint32_t s1) {
+        s_bin[b] = p;
+        s_lo[b] = s0;
+        s_hi[b] = s1;
+        if (p == ~0u || s1 - s0 > SB_CAP) return;  // none left / inconsistent plan (flagged by the CTA)
+        const uint32_t klo = s0 & ~3u, khi = (s1 + 3) & ~3u;
+        fence_proxy_async_smem();  // earlier reads and writes of the buffer come before the copy's writes
+        mbar_arrive_expect_tx(&s_bar[b], (khi - klo) * 4);
+        if (khi > klo) bulk_load(s_buf0 + b * SB_BUF_KEYS, in + klo, (khi - klo) * 4, &s_bar[b]);
+    };
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int b = 0; b < 2; ++b) {
+            const uint32_t it = blockIdx.x + b * G;
+            const uint32_t p = it < n_small ? __ldg(work + n_big + it) : ~0u;
+            start_copy(b, p, p != ~0u ? __ldg(bin_start + p) : 0u, p != ~0u ? __ldg(bin_start + p + 1) : 0u);
+        }
+    }
+    *reinterpret_cast<uint4*>(s_cnt + 8 * tid) = make_uint4(0, 0, 0, 0);
+    *reinterpret_cast<uint4*>(s_cnt + 8 * tid + 4) = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    uint32_t parity = 0;  // bit b: the phase buffer b's barrier completes next
+    bool failed = false, bad = false;
+    int b = 0;
+    for (uint32_t it = blockIdx.x; it < n_small; it += G, b ^= 1) {
+        const uint32_t p = s_bin[b];
+        const uint32_t s0 = s_lo[b], s1 = s_hi[b];
+        // (thread 0) the bin two ahead: its number now, its range after the histogram
+        const uint32_t it2 = it + 2 * G;
+        uint32_t p2 = ~0u, lo2 = 0, hi2 = 0;
+        if (tid == 0 && it2 < n_small) p2 = __ldg(work + n_big + it2);
+        const bool ok = s1 - s0 <= SB_CAP;
+        bad |= !ok;  // (inconsistent plan: nothing was copied)
+        if (ok) {
+            uint32_t polls = 0;
+            while (!mbar_test_parity(&s_bar[b], (parity >> b) & 1u) && ++polls < SB_WAIT_LIMIT) {
+            }
+            failed = polls >= SB_WAIT_LIMIT;
+            parity ^= 1u << b;
+        }
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        const uint32_t nk = ok ? s1 - s0 : 0u;
+        const uint32_t klo = s0 & ~3u;
+        const uint32_t a = s0 - klo;           // the bin's first key sits at buffer index a
+        const uint32_t nv = (a + nk + 3) / 4;  // 16-byte groups holding the bin
+        uint32_t* buf = s_buf0 + b * SB_BUF_KEYS;
+        const uint32_t b0 = p << BIN_SHIFT;
+        const uint32_t nb = POW2 ? BPB : (uint32_t)min((uint64_t)BPB, H.B - b0);
+        // histogram.  Thread t reads 16-byte groups t, t + 1024, ...; the bucket
+        // inside the bin of each key (13 bits; 0xffff = not a key of the bin) is
+        // kept in registers for the placement, two per word.
+        // (groups past the thread's last are skipped by a branch, which is the
+        // same for all lanes of a warp but the last one: no predicated-off work)
+        const uint32_t ng = nv > tid ? (nv - tid + SB_THREADS - 1) / SB_THREADS : 0u;
+        uint32_t key[SB_KPT], jw[2 * GR];
+#pragma unroll
+        for (int g = 0; g < GR; ++g) {
+            if ((uint32_t)g >= ng) break;
+            const uint32_t v = tid + (uint32_t)g * SB_THREADS;
+            {
+                const uint4 x = reinterpret_cast<const uint4*>(buf)[v];
+                key[4 * g] = x.x;
+                key[4 * g + 1] = x.y;
+                key[4 * g + 2] = x.z;
+                key[4 * g + 3] = x.w;
+                uint32_t js[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const bool in_bin = 4 * v + e - a < nk;
+                    // the words are the keys' hashes (the partition passes' output)
+                    const uint32_t h = key[4 * g + e];
+                    uint32_t j;
+                    if (POW2) {  // B = 2^k >= BPB: the bucket's low bits are its place in the bin
+                        j = h & (BPB - 1);
+                        bad |= in_bin && ((h & (uint32_t)H.mask) >> BIN_SHIFT) != p;
+                    } else {
+                        j = bucket_of_hash(h, H) - b0;
+                        bad |= in_bin && j >= nb;
+                        j = min(j, nb - 1);
+                    }
+                    if (in_bin) atomicAdd(s_cnt + j, 1u);
+                    js[e] = in_bin ? j : 0xffffu;
+                }
+                jw[2 * g] = js[0] | (js[1] << 16);
+                jw[2 * g + 1] = js[2] | (js[3] << 16);
+            }
+        }
+        if (tid == 0 && p2 != ~0u) {
+            lo2 = __ldg(bin_start + p2);
+            hi2 = __ldg(bin_start + p2 + 1);
+        }
+        __syncthreads();
+        // exclusive scan of the bin's counts: thread t owns buckets [8t, 8t + 8)
+        const uint32_t j0 = 8 * tid;
+        const uint4 c0 = *reinterpret_cast<const uint4*>(s_cnt + j0);
+        const uint4 c1 = *reinterpret_cast<const uint4*>(s_cnt + j0 + 4);
+        const uint32_t cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) tsum += cv[e];
+        const uint32_t winc = warp_inclusive_scan(tsum);
+        if (lane == 31) s_wsum[w] = winc;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t x = s_wsum[lane];
+            s_wsum[lane] = warp_inclusive_scan(x) - x;
+        }
+        __syncthreads();
+        uint32_t st[8];
+        st[0] = s_wsum[w] + winc - tsum;
+#pragma unroll
+        for (int e = 1; e < 8; ++e) st[e] = st[e - 1] + cv[e - 1];
+        if (ok) {
+            if (POW2 || j0 + 8 <= nb) {
+                uint4* o = reinterpret_cast<uint4*>(offsets + b0 + j0);
+                o[0] = make_uint4(s0 + st[0], s0 + st[1], s0 + st[2], s0 + st[3]);
+                o[1] = make_uint4(s0 + st[4], s0 + st[5], s0 + st[6], s0 + st[7]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (j0 + e < nb) offsets[b0 + j0 + e] = s0 + st[e];
+            }
+        }
+        if (LONGS && nk > SUM_MIN_LEN) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (cv[e] > SUM_MIN_LEN) note_long(LF, b0 + j0 + e);
+        }
+        // placement cursors, as buffer indices
+        *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(a + st[0], a + st[1], a + st[2], a + st[3]);
+        *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(a + st[4], a + st[5], a + st[6], a + st[7]);
+        __syncthreads();
+        // placement into the same buffer (every word is in registers now)
+#pragma unroll
+        for (int g = 0; g < GR; ++g) {
+            if ((uint32_t)g >= ng) break;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t j = (jw[2 * g + e / 2] >> (16 * (e & 1))) & 0xffffu;
+                if (j != 0xffffu) {
+                    const uint32_t pos = atomicAdd(s_cnt + j, 1u);
+                    bad |= pos - a >= nk;
+                    if (pos < SB_BUF_KEYS) buf[pos] = key[4 * g + e];
+                }
+            }
+        }
+        __syncthreads();
+        // the sorted bin out as keys (the words are hashes: fmix32_inv undoes them):
+        // 16-byte stores for the aligned body, single keys at the edges
+        if (ok) {
+            const uint32_t v0 = (s0 + 3) & ~3u, v1 = s1 & ~3u;  // aligned body [v0, v1) (empty if v1 <= v0)
+            if (v1 > v0) {
+                const uint32_t nvec = (v1 - v0) / 4;
+                const uint4* src = reinterpret_cast<const uint4*>(buf + (v0 - klo));
+                uint4* dst = reinterpret_cast<uint4*>(out + v0);
+                for (uint32_t v = tid; v < nvec; v += SB_THREADS) {
+                    const uint4 x = src[v];
+                    dst[v] = make_uint4(unhash_key32(x.x, H), unhash_key32(x.y, H), unhash_key32(x.z, H),
+                                        unhash_key32(x.w, H));
+                }
+                if (tid < v0 - s0) out[s0 + tid] = unhash_key32(buf[a + tid], H);
+                if (tid < s1 - v1) out[v1 + tid] = unhash_key32(buf[(v1 - klo) + tid], H);
+            } else if (tid < nk) {
+                out[s0 + tid] = unhash_key32(buf[a + tid], H);
+            }
+        }
+        *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+        if (tid == 0) start_copy(b, p2, lo2, hi2);  // the bin after next, into this buffer
+    }
+    if (bad) atomicOr(err, DEVERR_BOUNDS);
+    if (failed && tid == 0) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        // let the copies this CTA started finish (bounded) before it leaves
+        for (int c = 0; c < 2; ++c) {
+            if (s_bin[c] == ~0u || s_hi[c] - s_lo[c] > SB_CAP) continue;
+            uint32_t polls = 0;
+            while (!mbar_test_parity(&s_bar[c], (parity >> c) & 1u) && ++polls < SB_WAIT_LIMIT) {
+            }
+        }
+    }
+}
+
 size_t local_smem_bytes(size_t key_bytes, bool hv) {
     const size_t cap = LOCAL_STAGE_BYTES / (key_bytes + (hv ? 4 : 0));
     return (size_t)BPB * 4 + BPB / 8 + 2 * MAX_HOT * 4 + cap * (key_bytes + (hv ? 4 : 0));
@@ -1005,19 +1444,36 @@ unsigned grid_for(Kern kern, int threads, size_t smem) {
     return (unsigned)(num_sms() * per_sm);
 }
 
-template <typename K, int PM>
+// One partition pass.  32-bit keys take k_pass32 (HIN: the input is already
+// hashes; the output always is), 64-bit keys k_pass_down.  DR: record what the
+// reverse passes need (query grouping).
+template <typename K, int PM, bool HIN = false, bool DR = false>
 cudaError_t launch_down(const K* in, const uint32_t* in_v, uint64_t n, const Hasher& H, uint32_t dig_shift,
                         uint32_t dig_mask, uint32_t R, const ChunkMap& cm, uint32_t nch_host, uint32_t grid,
                         const Plan* plan, const uint32_t* base, K* out, uint32_t* out_v, uint32_t* err,
-                        cudaStream_t s) {
-    auto kern = k_pass_down<K, PM>;
-    const size_t smem = pass_smem_bytes<K>(PM != 0);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    launch_begin("part_scatter", s);
-    kern<<<grid, PASS_THREADS, smem, s>>>(in, in_v, n, H, dig_shift, dig_mask, R, cm, nch_host, plan, base, out, out_v,
-                                          err, nullptr, nullptr);
-    launch_end("part_scatter", s);
+                        cudaStream_t s, const char* name = "part_scatter", uint32_t* dr = nullptr,
+                        uint2* lb = nullptr, bool in_padded = false) {
+    cudaError_t e;
+    if constexpr (sizeof(K) == 4) {
+        auto kern = H.mode == MODE_POW2 ? k_pass32<HIN, PM, DR, true> : k_pass32<HIN, PM, DR, false>;
+        const size_t smem = (size_t)P32<PM>::TILE * (PM ? 8 : 4);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        launch_begin(name, s);
+        kern<<<grid, P32_THREADS, smem, s>>>(in, in_v, n, H, dig_shift, dig_mask, R, cm, nch_host, plan, base, out,
+                                             out_v, err, dr, lb, in_padded ? 1u : 0u);
+        launch_end(name, s);
+    } else {
+        static_assert(!HIN, "64-bit keys are never passed as hashes");
+        auto kern = k_pass_down<K, PM, DR>;
+        const size_t smem = pass_smem_bytes<K>(PM != 0);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        launch_begin(name, s);
+        kern<<<grid, PASS_THREADS, smem, s>>>(in, in_v, n, H, dig_shift, dig_mask, R, cm, nch_host, plan, base, out,
+                                              out_v, err, dr, lb);
+        launch_end(name, s);
+    }
     return cudaGetLastError();
 }
 
@@ -1099,9 +1555,14 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
             e = cudaGetLastError();
         }
     }
+    // 32-bit keys move through the passes as their hashes (k_pass32), so every
+    // kernel after the first pass reads hashes
+    constexpr bool HASHED = sizeof(K) == 4;
+    // 32-bit keys without values: bins of at most SB_CAP keys go to k_bin_small
+    const bool small_path = sizeof(K) == 4 && !hv;
     // 2. plan
     if (e == cudaSuccess) {
-        const uint32_t big_t = (uint32_t)(LOCAL_STAGE_BYTES / (sizeof(K) + (hv ? 4 : 0)));
+        const uint32_t big_t = small_path ? SB_CAP : (uint32_t)(LOCAL_STAGE_BYTES / (sizeof(K) + (hv ? 4 : 0)));
         launch_begin("part_plan", s);
         k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, n, big_t, bin_start, seg, work, huge_bin, huge_cs, plan,
                                        t.offsets, B);
@@ -1133,7 +1594,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     // 3b. second pass (bins inside each coarse segment)
     if (e == cudaSuccess && two) {
         launch_begin("chunk_count", s);
-        k_chunk_count<K><<<nch_b_max, PASS_THREADS, 0, s>>>(ka, t.H, cm_b, plan, cnt_b);
+        k_chunk_count<K, HASHED><<<nch_b_max, PASS_THREADS, 0, s>>>(ka, t.H, cm_b, plan, cnt_b);
         launch_end("chunk_count", s);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
@@ -1144,16 +1605,16 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
         }
         if (e == cudaSuccess) {
             if (hv)
-                e = launch_down<K, 1>(ka, va, n, t.H, 0, RADIX - 1, P2, cm_b, 0u, nch_b_max, plan, cnt_b, kb, vb,
-                                      t.err, s);
+                e = launch_down<K, 1, HASHED>(ka, va, n, t.H, 0, RADIX - 1, P2, cm_b, 0u, nch_b_max, plan, cnt_b, kb,
+                                              vb, t.err, s, "part_scatter2", nullptr, nullptr, true);
             else
-                e = launch_down<K, 0>(ka, nullptr, n, t.H, 0, RADIX - 1, P2, cm_b, 0u, nch_b_max, plan, cnt_b, kb,
-                                      nullptr, t.err, s);
+                e = launch_down<K, 0, HASHED>(ka, nullptr, n, t.H, 0, RADIX - 1, P2, cm_b, 0u, nch_b_max, plan, cnt_b,
+                                              kb, nullptr, t.err, s, "part_scatter2", nullptr, nullptr, true);
         }
     }
     // 4. huge bins: chunk histograms, then their offsets and cursors
     if (e == cudaSuccess) {
-        auto kern = k_huge_count<K>;
+        auto kern = k_huge_count<K, HASHED>;
         const size_t smem = (size_t)BPB * 4;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) {
@@ -1181,11 +1642,27 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
             launch_begin("bin_build", s);
             kern<<<grid_for(kern, LOCAL_THREADS, smem), LOCAL_THREADS, smem, s>>>(
                 kb, hv ? vb : nullptr, n, t.H, bin_start, work, huge_bin, huge_cs, plan, huge_cursor, ctr,
-                t.offsets, kout, t.values, t.err, t.finder);
+                t.offsets, kout, t.values, t.err, t.finder, small_path);
             launch_end("bin_build", s);
             return cudaGetLastError();
         };
-        e = hv ? run(k_bin_local<K, true>) : run(k_bin_local<K, false>);
+        e = hv ? run(k_bin_local<K, true, HASHED>) : run(k_bin_local<K, false, HASHED>);
+    }
+    if (e == cudaSuccess && small_path) {
+        auto run = [&](auto kern) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB_SMEM);
+            if (r != cudaSuccess) return r;
+            launch_begin("bin_small", s);
+            kern<<<grid_for(kern, SB_THREADS, SB_SMEM), SB_THREADS, SB_SMEM, s>>>(
+                reinterpret_cast<const uint32_t*>(kb), t.H, bin_start, work, plan, t.offsets,
+                static_cast<uint32_t*>(t.keys), t.err, t.finder);
+            launch_end("bin_small", s);
+            return cudaGetLastError();
+        };
+        if (t.H.mode == MODE_POW2 && t.B >= BPB)
+            e = t.finder.map ? run(k_bin_small<true, true>) : run(k_bin_small<true, false>);
+        else
+            e = t.finder.map ? run(k_bin_small<false, true>) : run(k_bin_small<false, false>);
     }
     dev_free(mem, s);
     return e;
@@ -1275,22 +1752,16 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
         launch_end("chunk_scan", s);
         e = cudaGetLastError();
     }
-    auto down = [&](const K* in, K* out, const ChunkMap& cm, uint32_t nch_host, uint32_t grid, uint32_t sh,
-                    uint32_t mask, uint32_t R, const uint32_t* cbase, uint32_t* dr, uint2* lb) {
-        auto kern = k_pass_down<K, 0, true>;
-        const size_t smem = pass_smem_bytes<K>(false);
-        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (r != cudaSuccess) return r;
-        launch_begin("q_partition", s);
-        kern<<<grid, PASS_THREADS, smem, s>>>(in, nullptr, nq, t.H, sh, mask, R, cm, nch_host, plan, cbase, out,
-                                              nullptr, (g->err ? g->err : t.err), dr, lb);
-        launch_end("q_partition", s);
-        return cudaGetLastError();
-    };
-    if (e == cudaSuccess) e = down(q, two ? qa : qb, cm_a, nch_a, nch_a, shift1, RADIX - 1, R1, cnt_a, dr_a, lb_a);
+    // 32-bit queries move through the passes as their hashes (k_pass32): the
+    // grouped queries are hashes, which the probes undo (items.qunhash)
+    constexpr bool HASHED = sizeof(K) == 4;
+    uint32_t* gerr = g->err ? g->err : t.err;
+    if (e == cudaSuccess)
+        e = launch_down<K, 0, false, true>(q, nullptr, nq, t.H, shift1, RADIX - 1, R1, cm_a, nch_a, nch_a, plan, cnt_a,
+                                           two ? qa : qb, nullptr, gerr, s, "q_partition", dr_a, lb_a);
     if (e == cudaSuccess && two) {
         launch_begin("chunk_count", s);
-        k_chunk_count<K><<<nch_b_max, PASS_THREADS, 0, s>>>(qa, t.H, cm_b, plan, cnt_b);
+        k_chunk_count<K, HASHED><<<nch_b_max, PASS_THREADS, 0, s>>>(qa, t.H, cm_b, plan, cnt_b);
         launch_end("chunk_count", s);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
@@ -1299,7 +1770,9 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
             launch_end("chunk_scan", s);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = down(qa, qb, cm_b, 0u, nch_b_max, 0, RADIX - 1, P2, cnt_b, dr_b, lb_b);
+        if (e == cudaSuccess)
+            e = launch_down<K, 0, HASHED, true>(qa, nullptr, nq, t.H, 0, RADIX - 1, P2, cm_b, 0u, nch_b_max, plan,
+                                                cnt_b, qb, nullptr, gerr, s, "q_partition2", dr_b, lb_b, true);
     }
     g->q_grouped = qb;
     g->bin_start = bin_start;
@@ -1317,6 +1790,7 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
     g->items.huge_chunk_start = reinterpret_cast<const uint32_t*>(base + o_hcs);
     g->items.work = reinterpret_cast<const uint32_t*>(base + o_work);
     g->items.huge_chunk = HUGE_CHUNK;
+    g->items.qunhash = HASHED ? ((1ull << 32) | (uint32_t)t.H.seed) : 0ull;
     g->dr_a = dr_a;
     g->dr_b = dr_b;
     g->lb_a = lb_a;

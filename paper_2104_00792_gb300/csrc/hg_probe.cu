@@ -39,7 +39,15 @@ struct LongList {
     uint32_t* mult;          // [cap] number of entries a walked entry answers
     uint32_t* cursor;        // [cap] gather write cursors (or null)
     uint32_t cap;
+    uint64_t qunhash = 0;    // the queries are hashes of 32-bit keys (BinWork::qunhash)
 };
+
+// A query as its key: grouped 32-bit queries are held as their hashes (qunhash
+// = 1 << 32 | seed), which fmix32_inv undoes; otherwise the word itself.
+__device__ __forceinline__ uint32_t query_key(uint32_t w, uint64_t qunhash) {
+    return (qunhash >> 32) ? fmix32_inv(w) ^ (uint32_t)qunhash : w;
+}
+__device__ __forceinline__ uint64_t query_key(uint64_t w, uint64_t) { return w; }
 constexpr uint32_t DEDUP_SLOTS = 16384;  // shared-memory hash table of k_long_prep
 
 // The part of a LongList the probe kernels append to.
@@ -311,7 +319,7 @@ k_long_prep(const K* __restrict__ qs, const uint32_t* __restrict__ offs, Hasher 
         for (uint32_t i = threadIdx.x; i < DEDUP_SLOTS; i += blockDim.x) s_ht[i] = ~0ull;
         __syncthreads();
         for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-            const uint32_t key = (uint32_t)qs[L.slot[e]];
+            const uint32_t key = (uint32_t)query_key(qs[L.slot[e]], L.qunhash);
             uint32_t h = fmix32(key ^ 0x9e3779b9u) & (DEDUP_SLOTS - 1);
             uint32_t r = e;
             for (uint32_t probe = 0; probe < DEDUP_SLOTS; ++probe) {
@@ -365,7 +373,7 @@ k_long_prep(const K* __restrict__ qs, const uint32_t* __restrict__ offs, Hasher 
         const uint32_t u = base + threadIdx.x;
         uint64_t ch = 0;
         if (u < nu) {
-            const uint32_t b = bucket_of(qs[L.slot[L.uniq[u]]], H);
+            const uint32_t b = bucket_of(query_key(qs[L.slot[L.uniq[u]]], L.qunhash), H);
             const uint32_t hi = min(offs[b + 1], n_keys);
             const uint32_t lo = min(offs[b], hi);
             ch = (hi - lo + LONG_CHUNK - 1) / LONG_CHUNK;
@@ -412,7 +420,7 @@ k_long(const K* __restrict__ qs, const K* __restrict__ keys, const uint32_t* __r
         const uint32_t u = lo;
         const uint32_t e = L.uniq[u];
         const uint32_t s = L.slot[e];
-        const K key = qs[s];
+        const K key = query_key(qs[s], L.qunhash);
         const uint32_t b = bucket_of(key, H);
         const uint64_t l1 = min(offs[b + 1], n_keys);
         const uint64_t l0 = min((uint64_t)offs[b], l1);
@@ -725,11 +733,12 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
         const uint64_t b0 = (uint64_t)p * BIN_BUCKETS;
         const uint32_t nb = (uint32_t)min((uint64_t)BIN_BUCKETS, B - b0);
         // each warp answers 32 queries at a time; the next 32 are loaded meanwhile
+        // (raw words: a grouped query becomes its key where it is used, so the load stays in flight)
         K key_next = (q0 + warp * 32 + lane < q1) ? __ldg(qs + q0 + warp * 32 + lane) : (K)0;
         for (uint32_t i0 = q0 + warp * 32; i0 < q1; i0 += nwarps * 32) {
             const uint32_t i = i0 + lane;
             const bool ok = i < q1;
-            const K key = key_next;
+            const K key = query_key(key_next, W.qunhash);
             {
                 const uint32_t inext = i + nwarps * 32;
                 key_next = inext < q1 ? __ldg(qs + inext) : (K)0;
@@ -863,12 +872,13 @@ constexpr int HJ_QUNROLL = 4;                         // query loads in flight p
 constexpr uint32_t HJ_MAX_LONG = 8;                   // long buckets of a hot bin (segments: one more)
 static_assert(HJ_KEY_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
 
-// first slot (top 12 bits of a mix of the key) and probe step (odd, so the
-// sequence visits every slot of the power-of-two table)
-__device__ __forceinline__ void hj_probe_seq(uint32_t k, uint32_t& slot, uint32_t& step) {
-    uint32_t x = k * 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
+// First slot and probe step (odd, so the sequence visits every slot of the
+// power-of-two table) of a key's hash h.  h is already well mixed, but the keys
+// of one bin share the bits that name the bin, so the slot is taken from the
+// top bits of h times 2^32 / golden ratio (Knuth's multiplicative hashing,
+// TAOCP vol. 3, Sec. 6.4), which depend on every bit of h.
+__device__ __forceinline__ void hj_probe_seq(uint32_t h, uint32_t& slot, uint32_t& step) {
+    const uint32_t x = h * 0x9e3779b1u;
     slot = x >> (32 - 12);
     step = (x >> 7) | 1u;
 }
@@ -879,7 +889,8 @@ __global__ void __launch_bounds__(HJ_THREADS, 2)
 k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_start, BinWork W,
              const uint32_t* __restrict__ keys, const uint32_t* __restrict__ offs, uint64_t B, uint32_t n_keys,
              void* counts, uint64_t* total, uint32_t* work_ctr, uint32_t* fb_list, uint32_t* fb_n, uint32_t* tries,
-             uint32_t* err, LongSummary S) {
+             uint32_t* err, LongSummary S, uint32_t hseed) {
+    const bool qhashed = (W.qunhash >> 32) != 0;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long* s_ht = reinterpret_cast<unsigned long long*>(smem);
     unsigned char* const s_buf = smem + HJ_SLOTS * 8;
@@ -1074,11 +1085,14 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
 #pragma unroll
         for (int u = 0; u < HJ_QUNROLL; ++u) {
             const uint32_t i = q0 + u * blockDim.x + threadIdx.x;
-            kq[u] = i < q1 ? __ldg(qs + i) : 0u;
+            kq[u] = i < q1 ? __ldg(qs + i) : 0u;  // raw words, made keys where they are used
         }
         // count the bin's keys: runs of equal keys inside each 32-key step, one
         // insert per run; two steps per iteration for independent loads
-        auto insert = [&](uint32_t k, uint32_t len) {
+        // the table holds each key's hash h = fmix32(k ^ seed) (a bijection, so
+        // equal hashes are equal keys), the form in which the grouped queries come
+        auto insert = [&](uint32_t key, uint32_t len) {
+            const uint32_t k = fmix32(key ^ hseed);
             const unsigned long long add = (unsigned long long)len << 32;
             uint32_t sl, stp;
             hj_probe_seq(k, sl, stp);
@@ -1157,12 +1171,14 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
                 for (int u = 0; u < HJ_QUNROLL; ++u) {
                     const uint32_t i = g0 + u * blockDim.x + threadIdx.x;
                     if (i < q1) {
+                        // the query's hash (grouped 32-bit queries already are hashes)
+                        const uint32_t qk = qhashed ? kq[u] : fmix32(kq[u] ^ hseed);
                         uint32_t sl, stp, cnt = 0;
-                        hj_probe_seq(kq[u], sl, stp);
+                        hj_probe_seq(qk, sl, stp);
                         for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
                             const unsigned long long w = s_ht[sl];
                             if (w == 0ull) break;
-                            if ((uint32_t)w == kq[u]) {
+                            if ((uint32_t)w == qk) {
                                 cnt = (uint32_t)(w >> 32);
                                 break;
                             }
@@ -1208,7 +1224,8 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
             per_sm = 1;
         launch_begin("probe_hash", s);
         kern<<<num_sms() * per_sm, HJ_THREADS, smem, s>>>(qs, g.bin_start, g.items, keys, t.offsets, t.B, (uint32_t)t.n,
-                                                          counts, total, ctrs, fb_list, ctrs + 2, ctrs + 3, t.err, t.sum);
+                                                          counts, total, ctrs, fb_list, ctrs + 2, ctrs + 3, t.err, t.sum,
+                                                          (uint32_t)t.H.seed);
         launch_end("probe_hash", s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1252,6 +1269,7 @@ cudaError_t count_grouped(const Table& t, const GroupedQueries& g, uint64_t q, u
     const uint32_t cap = (uint32_t)(q < COUNT_LONG_CAP ? q : COUNT_LONG_CAP);
     cudaError_t e = alloc_list(cap, false, s, &mem, &L);
     if (e != cudaSuccess) return e;
+    L.qunhash = g.items.qunhash;
     void* cmem = nullptr;
     const size_t cbytes = ((q + 4) * 4 + 255) & ~size_t(255);
     // the hash join's fallback list: at most one entry per work item
