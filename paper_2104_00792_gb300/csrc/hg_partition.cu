@@ -21,7 +21,7 @@
 //                    contiguous runs.  When a bin does not fit, its largest
 //                    buckets go straight to global memory (their keys land on
 //                    consecutive positions) and the rest is staged.
-//      Bins above HUGE_T keys are split over many CTAs: k_huge_count ->
+//      Bins above HUGE_T_BUILD keys are split over many CTAs: k_huge_count ->
 //      k_huge_scan -> chunk placement through per-bucket cursors.
 // The result equals the direct build's (offsets bit-exact; the order inside
 // a bucket differs, which Algorithm 1 leaves free).
@@ -44,7 +44,8 @@ constexpr uint32_t CHUNK = 1u << 16;        // keys per reduce-then-scan chunk
 constexpr uint32_t TILES_PER_CHUNK = CHUNK / 2048;  // upper bound for either key width
 constexpr uint32_t MAX_HOT = 256;           // buckets per bin that may bypass the staging buffer
 constexpr size_t LOCAL_STAGE_BYTES = 72 * 1024;
-constexpr uint32_t HUGE_T = 1u << 18;       // bins with more keys are split over many CTAs
+constexpr uint32_t HUGE_T = 1u << 18;       // query bins with more queries are cut into work items
+constexpr uint32_t HUGE_T_BUILD = 1u << 16; // build bins with more keys are split over many CTAs
 constexpr uint32_t HUGE_CHUNK = 1u << 16;   // keys per CTA work item of a huge bin
 constexpr uint32_t MAX_HUGE = 512;          // huge bins with their own counter/cursor slice
 constexpr int NTHR = 5;                     // candidate hot-bucket thresholds
@@ -258,11 +259,11 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T* total) {
 
 // One CTA.  Writes bin_start[P+1]; seg_chunk_start[P1+1] (chunks of each
 // coarse segment in the second pass); offsets[B] = n; the huge bins (more
-// than HUGE_T keys; the first MAX_HUGE of them) with the prefix of their
+// than huge_t keys; the first MAX_HUGE of them) with the prefix of their
 // chunk counts; and the work list of the other bins, bins above big_t keys first.
 __global__ void __launch_bounds__(1024)
 k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uint32_t P2, uint64_t n,
-            uint32_t big_t, uint32_t* bin_start, uint32_t* seg_chunk_start, uint32_t* work, uint32_t* huge_bin,
+            uint32_t big_t, uint32_t huge_t, uint32_t* bin_start, uint32_t* seg_chunk_start, uint32_t* work, uint32_t* huge_bin,
             uint32_t* huge_chunk_start, Plan* plan, uint32_t* offsets, uint64_t B) {
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_huge[MAX_BINS / 32];
@@ -299,7 +300,7 @@ k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uin
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t p = base + threadIdx.x;
         const uint32_t c = p < P ? bin_count[p] : 0u;
-        const uint32_t is_huge = c > HUGE_T ? 1u : 0u;
+        const uint32_t is_huge = c > huge_t ? 1u : 0u;
         const uint32_t hx = block_exclusive_scan<uint32_t>(is_huge, s_warp, &tot);
         const bool admit = is_huge && nh + hx < MAX_HUGE;
         const uint32_t ch = admit ? (c + HUGE_CHUNK - 1) / HUGE_CHUNK : 0u;
@@ -1564,8 +1565,8 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     if (e == cudaSuccess) {
         const uint32_t big_t = small_path ? SB_CAP : (uint32_t)(LOCAL_STAGE_BYTES / (sizeof(K) + (hv ? 4 : 0)));
         launch_begin("part_plan", s);
-        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, n, big_t, bin_start, seg, work, huge_bin, huge_cs, plan,
-                                       t.offsets, B);
+        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, n, big_t, HUGE_T_BUILD, bin_start, seg, work, huge_bin,
+                                       huge_cs, plan, t.offsets, B);
         launch_end("part_plan", s);
         e = cudaGetLastError();
     }
@@ -1739,7 +1740,7 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
         launch_begin("part_plan", s);
         // bins of many queries first in the probe's work list; the bins with the
         // most (huge bins) are cut into HUGE_CHUNK-query work items
-        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, nq, 1u << 16, bin_start, seg,
+        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, nq, 1u << 16, HUGE_T, bin_start, seg,
                                        reinterpret_cast<uint32_t*>(base + o_work),
                                        reinterpret_cast<uint32_t*>(base + o_hbin),
                                        reinterpret_cast<uint32_t*>(base + o_hcs), plan, nullptr, B);
