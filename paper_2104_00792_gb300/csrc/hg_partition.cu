@@ -149,10 +149,11 @@ __device__ __forceinline__ void block_for_range(const K* __restrict__ in, const 
 // ------------------------------------------------------------- chunking --
 struct Plan {
     uint32_t chunks_b;     // chunks of the second pass
-    uint32_t n_huge;       // bins split over many CTAs (at most MAX_HUGE)
-    uint32_t huge_chunks;  // their HUGE_CHUNK-key work items
+    uint32_t n_huge;       // bins split over many CTAs (at most the plan's max_huge)
+    uint32_t huge_chunks;  // their huge_chunk-key work items
     uint32_t n_work;       // bins handled whole by one CTA
     uint32_t n_big;        // the first n_big of them hold more than the plan's big_t keys
+    uint32_t huge_chunk;   // keys per work item of a huge bin
 };
 
 // Chunk c of a pass: keys [lo, hi) of segment `seg`.  Single-segment passes
@@ -259,11 +260,11 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T* total) {
 
 // One CTA.  Writes bin_start[P+1]; seg_chunk_start[P1+1] (chunks of each
 // coarse segment in the second pass); offsets[B] = n; the huge bins (more
-// than huge_t keys; the first MAX_HUGE of them) with the prefix of their
+// than huge_t keys; the first max_huge of them) with the prefix of their
 // chunk counts; and the work list of the other bins, bins above big_t keys first.
 __global__ void __launch_bounds__(1024)
 k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uint32_t P2, uint64_t n,
-            uint32_t big_t, uint32_t huge_t, uint32_t* bin_start, uint32_t* seg_chunk_start, uint32_t* work, uint32_t* huge_bin,
+            uint32_t big_t, uint32_t huge_t, uint32_t huge_chunk, uint32_t max_huge, uint32_t* bin_start, uint32_t* seg_chunk_start, uint32_t* work, uint32_t* huge_bin,
             uint32_t* huge_chunk_start, Plan* plan, uint32_t* offsets, uint64_t B) {
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_huge[MAX_BINS / 32];
@@ -295,15 +296,15 @@ k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uin
         if (sg < P1) seg_chunk_start[sg] = crun + ex;
         crun += tot;
     }
-    // huge bins (index order, first MAX_HUGE) and their chunk prefix
+    // huge bins (index order, first max_huge) and their chunk prefix
     uint32_t nh = 0, cr = 0;
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t p = base + threadIdx.x;
         const uint32_t c = p < P ? bin_count[p] : 0u;
         const uint32_t is_huge = c > huge_t ? 1u : 0u;
         const uint32_t hx = block_exclusive_scan<uint32_t>(is_huge, s_warp, &tot);
-        const bool admit = is_huge && nh + hx < MAX_HUGE;
-        const uint32_t ch = admit ? (c + HUGE_CHUNK - 1) / HUGE_CHUNK : 0u;
+        const bool admit = is_huge && nh + hx < max_huge;
+        const uint32_t ch = admit ? (c + huge_chunk - 1) / huge_chunk : 0u;
         uint32_t ctot;
         const uint32_t cx = block_exclusive_scan<uint32_t>(ch, s_warp, &ctot);
         if (admit) {
@@ -314,7 +315,7 @@ k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uin
         nh += tot;
         cr += ctot;
     }
-    const uint32_t n_huge = min(nh, MAX_HUGE);
+    const uint32_t n_huge = min(nh, max_huge);
     __syncthreads();
     // work list: big bins first, then the rest
     uint32_t nbig = 0;
@@ -343,6 +344,7 @@ k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uin
         plan->huge_chunks = cr;
         plan->n_work = nbig + nsmall;
         plan->n_big = nbig;
+        plan->huge_chunk = huge_chunk;
     }
 }
 
@@ -825,9 +827,112 @@ k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, Chu
     }
 }
 
+// k_pass_reverse for the 32-bit passes (k_pass32): 256 threads, each holding
+// 32 elements of a tile as eight 4-element groups (element x of the chunk's
+// window in thread (x / 4) % 256, as in the forward pass), so the records come
+// in and the values go out 16 bytes at a time.
+__global__ void __launch_bounds__(P32_THREADS, 3)
+k_pass_reverse32(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, ChunkMap cm, uint32_t nch_host,
+                 const Plan* __restrict__ plan, const uint32_t* __restrict__ dr_in, const uint2* __restrict__ tile_lb,
+                 uint32_t* err) {
+    constexpr int TILE = P32<0>::TILE;
+    constexpr int NG = P32<0>::IPT / 4;
+    constexpr int PER = P32<0>::IPT;
+    __shared__ __align__(16) uint32_t s_val[TILE];
+    __shared__ uint8_t s_dig[TILE];
+    __shared__ uint2 s_lb[RADIX];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
+    const uint32_t c = blockIdx.x;
+    if (c >= nch) return;
+    uint32_t seg, first;
+    uint64_t lo, hi;
+    chunk_range(cm, c, seg, first, lo, hi);
+    // the forward pass's tiles over the chunk's window: position x is element
+    // lo - a + x, valid for a <= x < end
+    const uint32_t a = (uint32_t)(lo & 3);
+    const uint32_t end = a + (uint32_t)(hi - lo);
+    const uint32_t* __restrict__ drc = dr_in + (lo - a);  // (records: an internal array, padded and aligned)
+    uint32_t* __restrict__ dstc = dst + (lo - a);
+    const bool dvec = (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+    const uint2* __restrict__ lbc = tile_lb + (uint64_t)c * TILES_PER_CHUNK * RADIX;
+    uint32_t drs[PER];
+    uint2 lbr = make_uint2(0, 0);
+    auto fetch = [&](uint32_t t0) {
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const uint32_t x0 = t0 + (tid + g * P32_THREADS) * 4;
+            if (x0 < end) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4*>(drc + x0));
+                drs[4 * g] = x0 >= a ? q.x : 0xffffffffu;
+                drs[4 * g + 1] = x0 + 1 >= a && x0 + 1 < end ? q.y : 0xffffffffu;
+                drs[4 * g + 2] = x0 + 2 >= a && x0 + 2 < end ? q.z : 0xffffffffu;
+                drs[4 * g + 3] = x0 + 3 < end ? q.w : 0xffffffffu;
+            } else {
+                drs[4 * g] = drs[4 * g + 1] = drs[4 * g + 2] = drs[4 * g + 3] = 0xffffffffu;
+            }
+        }
+        if (tid < RADIX) lbr = __ldg(lbc + (t0 / TILE) * RADIX + tid);
+    };
+    if (end > a) fetch(0);
+    for (uint32_t t0 = 0; t0 < end; t0 += TILE) {
+        const uint32_t cnt_tile = min(end, t0 + (uint32_t)TILE) - max(a, t0);  // valid elements
+        if (tid < RADIX) s_lb[tid] = lbr;
+        __syncthreads();
+        // every element marks its staging position with its digit ...
+        static_assert(TILE < 0xffff, "staging positions are kept in 16 bits");
+        uint32_t pj[PER / 2];  // two 16-bit staging positions per word, 0xffff = none
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            uint32_t pos = 0xffffu;
+            if (drs[j] != 0xffffffffu) {
+                const uint32_t p = s_lb[drs[j] & 0xffu].x + (drs[j] >> 8);
+                if (p < (uint32_t)TILE) {
+                    s_dig[p] = (uint8_t)(drs[j] & 0xffu);
+                    pos = p;
+                } else {
+                    atomicOr(err, DEVERR_BOUNDS);
+                }
+            }
+            if (j & 1) pj[j / 2] |= pos << 16;
+            else pj[j / 2] = pos;
+        }
+        __syncthreads();
+        // ... so that the tile's runs are read back contiguously in staging order
+        // (asynchronous copies straight into shared memory)
+        for (uint32_t i = tid; i < cnt_tile; i += P32_THREADS) {
+            const uint2 lb = s_lb[s_dig[i]];
+            cp_async4(s_val + i, src + lb.y + (i - lb.x));
+        }
+        const uint32_t t1 = t0 + TILE;
+        if (t1 < end) fetch(t1);
+        cp_async_wait_all();
+        __syncthreads();
+        // s_lb and s_dig are not read past this point, and s_val is next written
+        // after the next tile's second barrier, so no barrier ends the tile
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const uint32_t x0 = t0 + (tid + g * P32_THREADS) * 4;
+            uint32_t pos[4], val[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                pos[u] = (pj[(4 * g + u) / 2] >> (((4 * g + u) & 1) * 16)) & 0xffffu;
+                val[u] = pos[u] != 0xffffu ? s_val[pos[u]] : 0u;
+            }
+            if (dvec && pos[0] != 0xffffu && pos[3] != 0xffffu) {
+                *reinterpret_cast<uint4*>(dstc + x0) = make_uint4(val[0], val[1], val[2], val[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (pos[u] != 0xffffu) dstc[x0 + u] = val[u];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- local --
 // Huge bin work item -> (huge index e, bin p, key range [c0, c1)).
-__device__ __forceinline__ void huge_item(uint32_t item, uint32_t n_huge, const uint32_t* __restrict__ huge_chunk_start,
+__device__ __forceinline__ void huge_item(uint32_t item, uint32_t n_huge, uint32_t chunk, const uint32_t* __restrict__ huge_chunk_start,
                                           const uint32_t* __restrict__ huge_bin,
                                           const uint32_t* __restrict__ bin_start, uint32_t& e, uint32_t& p,
                                           uint64_t& c0, uint64_t& c1) {
@@ -838,8 +943,8 @@ __device__ __forceinline__ void huge_item(uint32_t item, uint32_t n_huge, const 
     }
     e = lo;
     p = huge_bin[e];
-    c0 = (uint64_t)bin_start[p] + (uint64_t)(item - huge_chunk_start[e]) * HUGE_CHUNK;
-    c1 = min((uint64_t)bin_start[p + 1], c0 + HUGE_CHUNK);
+    c0 = (uint64_t)bin_start[p] + (uint64_t)(item - huge_chunk_start[e]) * chunk;
+    c1 = min((uint64_t)bin_start[p + 1], c0 + chunk);
 }
 
 // Huge bins, step 1: per-chunk bucket histograms added into huge_count[e][*].
@@ -866,7 +971,7 @@ k_huge_count(const K* __restrict__ in, Hasher H, const uint32_t* __restrict__ bi
     for (uint32_t item = blockIdx.x; item < total; item += gridDim.x) {
         uint32_t e, p;
         uint64_t c0, c1;
-        huge_item(item, n_huge, huge_chunk_start, huge_bin, bin_start, e, p, c0, c1);
+        huge_item(item, n_huge, plan->huge_chunk, huge_chunk_start, huge_bin, bin_start, e, p, c0, c1);
         const uint64_t b0 = (uint64_t)p << BIN_SHIFT;
         const uint32_t nb = (uint32_t)min((uint64_t)BPB, H.B - b0);
         for (uint32_t j = threadIdx.x; j < BPB; j += blockDim.x) s_cnt[j] = 0;
@@ -886,15 +991,26 @@ k_huge_count(const K* __restrict__ in, Hasher H, const uint32_t* __restrict__ bi
     }
 }
 
-// Huge bins, step 2: one CTA per huge bin scans its counts into offsets and cursors.
+// Huge bins, step 2: one CTA per huge bin scans its counts into offsets and
+// cursors; with item_meta, it also lists its work items as (bin slot e, bin p,
+// first key, end key).
 __global__ void __launch_bounds__(1024)
 k_huge_scan(const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ huge_bin,
-            const Plan* __restrict__ plan, const uint32_t* __restrict__ huge_count, uint32_t* huge_cursor,
-            uint32_t* offsets, uint64_t B, LongFinder LF) {
+            const uint32_t* __restrict__ huge_chunk_start, const Plan* __restrict__ plan,
+            const uint32_t* __restrict__ huge_count, uint32_t* huge_cursor, uint32_t* offsets, uint64_t B,
+            LongFinder LF, uint4* item_meta) {
     __shared__ uint32_t s_warp[33];
     const uint32_t e = blockIdx.x;
     if (e >= plan->n_huge) return;
     const uint32_t p = huge_bin[e];
+    if (item_meta) {
+        const uint32_t chunk = plan->huge_chunk, bs = bin_start[p], be = bin_start[p + 1];
+        const uint32_t i0 = huge_chunk_start[e], ni = huge_chunk_start[e + 1] - i0;
+        for (uint32_t k = threadIdx.x; k < ni; k += blockDim.x) {
+            const uint32_t lo = bs + k * chunk;
+            item_meta[i0 + k] = make_uint4(e, p, lo, min(be, lo + chunk));
+        }
+    }
     const uint64_t b0 = (uint64_t)p << BIN_SHIFT;
     const uint32_t nb = (uint32_t)min((uint64_t)BPB, B - b0);
     uint32_t running = bin_start[p], tot;
@@ -922,6 +1038,7 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             const uint32_t* __restrict__ huge_bin, const uint32_t* __restrict__ huge_chunk_start,
             const Plan* __restrict__ plan, uint32_t* huge_cursor, uint32_t* work_ctr, uint32_t* offsets,
             K* __restrict__ out, uint32_t* __restrict__ out_v, uint32_t* err, LongFinder LF, bool big_only) {
+    // big_only: k_bin_small takes the small bins and k_big_place the huge bins' chunks
     constexpr uint32_t STAGE_CAP = (uint32_t)(LOCAL_STAGE_BYTES / (sizeof(K) + (HV ? 4 : 0)));
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
@@ -937,12 +1054,13 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
     constexpr int NW = LOCAL_THREADS / 32;
     const uint64_t B = H.B;
     const uint32_t n_huge = plan->n_huge, huge_chunks = plan->huge_chunks;
-    const uint32_t n_work = big_only ? plan->n_big : plan->n_work;  // big_only: k_bin_small takes the rest
+    const uint32_t n_work = big_only ? plan->n_big : plan->n_work;
+    const uint32_t first_item = big_only ? huge_chunks : 0u;
     // candidate thresholds: a bucket with at least THR[k] keys bypasses the staging buffer
     const uint32_t THR[NTHR] = {0xffffffffu, 4096u, 1024u, 256u, 64u};
 
     while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(work_ctr, 1u);
+        if (threadIdx.x == 0) s_item = first_item + atomicAdd(work_ctr, 1u);
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= huge_chunks + n_work) break;
@@ -951,7 +1069,7 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
             // ---- one chunk of a huge bin: local histogram, reserve runs, place
             uint32_t e, p;
             uint64_t c0, c1;
-            huge_item(item, n_huge, huge_chunk_start, huge_bin, bin_start, e, p, c0, c1);
+            huge_item(item, n_huge, plan->huge_chunk, huge_chunk_start, huge_bin, bin_start, e, p, c0, c1);
             const uint64_t b0 = (uint64_t)p << BIN_SHIFT;
             const uint32_t nb = (uint32_t)min((uint64_t)BPB, B - b0);
             for (uint32_t j = threadIdx.x; j < BPB; j += blockDim.x) s_cnt[j] = 0;
@@ -1211,7 +1329,10 @@ k_bin_local(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
 // registers by then), and the sorted bin leaves in 16-byte stores.
 constexpr int SB_THREADS = 1024;
 constexpr int SB_KPT = 20;
-constexpr uint32_t SB_CAP = (uint32_t)SB_THREADS * SB_KPT;
+// A bin's (or chunk's) words are read from the 16-byte boundary at or before
+// its start, so up to 3 words before it share the threads' SB_THREADS * SB_KPT
+// slots: SB_CAP keys at most.
+constexpr uint32_t SB_CAP = (uint32_t)SB_THREADS * SB_KPT - 4;
 constexpr uint32_t SB_BUF_KEYS = SB_CAP + 8;        // room for the copy's 16-byte alignment at both ends
 constexpr uint32_t SB_WAIT_LIMIT = 1u << 24;        // polls of a copy's barrier before the CTA gives up
 constexpr size_t SB_SMEM = (size_t)BPB * 4 + 2 * (size_t)SB_BUF_KEYS * 4;
@@ -1425,6 +1546,184 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
     }
 }
 
+// Work items of the bins of more than SB_CAP 32-bit keys (no values): chunks of
+// SB_CAP words, their buckets pre-counted (k_huge_count) and turned into
+// offsets and per-bucket cursors (k_huge_scan).  Each CTA takes chunks
+// blockIdx.x, blockIdx.x + G, ... whose words arrive by bulk copies (TMA) two
+// chunks ahead, as in k_bin_small; per chunk: a shared-memory histogram, one
+// global atomic per nonempty bucket to reserve the chunk's run in it, and each
+// key written at its place.  These bins hold the most duplicated keys: the
+// lanes of a warp whose keys fall in the chunk's fullest bucket share one
+// atomic, and their keys go out as consecutive words.
+constexpr uint32_t MAX_HUGE_SB = 1536;  // bins of more than SB_CAP keys with a counter/cursor slice
+
+template <bool POW2>
+__global__ void __launch_bounds__(SB_THREADS, 1)
+k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__ item_meta,
+            const Plan* __restrict__ plan, uint32_t* __restrict__ huge_cursor, uint64_t n,
+            uint32_t* __restrict__ out, uint32_t* err) {
+    constexpr int GR = SB_KPT / 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* const s_buf0 = s_cnt + BPB;  // buffer b at s_buf0 + b * SB_BUF_KEYS
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_e[2], s_p[2], s_lo[2], s_hi[2], s_wmax[SB_THREADS / 32], s_hot;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+    const uint32_t items = plan->huge_chunks;
+    const uint32_t G = gridDim.x;
+    const uint32_t nn = (uint32_t)min(n, (uint64_t)0xffffffffu);
+
+    // thread 0: chunk (e, p, lo, hi) into buffer b (e = ~0u: none); its description
+    // is read one chunk ahead, so no phase waits on it
+    auto start_copy = [&](int b, uint4 m) {
+        const uint32_t e = m.x, p = m.y, lo = m.z, hi = m.w;
+        s_e[b] = e;
+        s_p[b] = p;
+        s_lo[b] = lo;
+        s_hi[b] = hi;
+        if (e == ~0u || hi - lo > SB_CAP) return;  // none left / inconsistent plan (flagged by the CTA)
+        const uint32_t klo = lo & ~3u, khi = (hi + 3) & ~3u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar[b], (khi - klo) * 4);
+        if (khi > klo) bulk_load(s_buf0 + b * SB_BUF_KEYS, in + klo, (khi - klo) * 4, &s_bar[b]);
+    };
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const uint4 none = make_uint4(~0u, 0, 0, 0);
+        start_copy(0, blockIdx.x < items ? item_meta[blockIdx.x] : none);
+        start_copy(1, blockIdx.x + G < items ? item_meta[blockIdx.x + G] : none);
+    }
+    *reinterpret_cast<uint4*>(s_cnt + 8 * tid) = make_uint4(0, 0, 0, 0);
+    *reinterpret_cast<uint4*>(s_cnt + 8 * tid + 4) = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    uint32_t parity = 0;
+    bool failed = false, bad = false;
+    int b = 0;
+    for (uint32_t it = blockIdx.x; it < items; it += G, b ^= 1) {
+        const uint32_t e = s_e[b], p = s_p[b], s0 = s_lo[b], s1 = s_hi[b];
+        uint4 m2 = make_uint4(~0u, 0, 0, 0);  // (thread 0) the chunk after next
+        if (tid == 0 && it + 2 * G < items) m2 = item_meta[it + 2 * G];
+        const bool ok = e != ~0u && s1 - s0 <= SB_CAP;
+        bad |= !ok;
+        if (ok) {
+            uint32_t polls = 0;
+            while (!mbar_test_parity(&s_bar[b], (parity >> b) & 1u) && ++polls < SB_WAIT_LIMIT) {
+            }
+            failed = polls >= SB_WAIT_LIMIT;
+            parity ^= 1u << b;
+        }
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        const uint32_t nk = ok ? s1 - s0 : 0u;
+        const uint32_t klo = s0 & ~3u, a = s0 - klo, nv = (a + nk + 3) / 4;
+        const uint32_t* buf = s_buf0 + b * SB_BUF_KEYS;
+        const uint32_t b0 = p << BIN_SHIFT;
+        const uint32_t nb = POW2 ? BPB : (uint32_t)min((uint64_t)BPB, H.B - b0);
+        const uint32_t ng = nv > tid ? (nv - tid + SB_THREADS - 1) / SB_THREADS : 0u;
+        uint32_t key[SB_KPT], jw[2 * GR];
+        // histogram of the chunk's buckets (the words are the keys' hashes)
+#pragma unroll
+        for (int g = 0; g < GR; ++g) {
+            if ((uint32_t)g >= ng) break;
+            const uint32_t v = tid + (uint32_t)g * SB_THREADS;
+            const uint4 x = reinterpret_cast<const uint4*>(buf)[v];
+            key[4 * g] = x.x;
+            key[4 * g + 1] = x.y;
+            key[4 * g + 2] = x.z;
+            key[4 * g + 3] = x.w;
+            uint32_t js[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool in_bin = 4 * v + u - a < nk;
+                const uint32_t h = key[4 * g + u];
+                uint32_t j;
+                if (POW2) {
+                    j = h & (BPB - 1);
+                    bad |= in_bin && ((h & (uint32_t)H.mask) >> BIN_SHIFT) != p;
+                } else {
+                    j = bucket_of_hash(h, H) - b0;
+                    bad |= in_bin && j >= nb;
+                    j = min(j, nb - 1);
+                }
+                if (in_bin) atomicAdd(s_cnt + j, 1u);
+                js[u] = in_bin ? j : 0xffffu;
+            }
+            jw[2 * g] = js[0] | (js[1] << 16);
+            jw[2 * g + 1] = js[2] | (js[3] << 16);
+        }
+        __syncthreads();
+        // reserve the chunk's run in every bucket it touches; thread t owns buckets [8t, 8t + 8)
+        const uint32_t j0 = 8 * tid;
+        {
+            const uint4 c0 = *reinterpret_cast<const uint4*>(s_cnt + j0);
+            const uint4 c1 = *reinterpret_cast<const uint4*>(s_cnt + j0 + 4);
+            const uint32_t cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            uint32_t base[8], cmax = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                base[u] = cv[u] ? atomicAdd(huge_cursor + (uint64_t)e * BPB + j0 + u, cv[u]) : 0u;
+                cmax = max(cmax, (cv[u] << BIN_SHIFT) | (j0 + u));
+            }
+            *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(base[0], base[1], base[2], base[3]);
+            *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(base[4], base[5], base[6], base[7]);
+            cmax = __reduce_max_sync(FULL_MASK, cmax);
+            if (lane == 0) s_wmax[w] = cmax;
+        }
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t m = __reduce_max_sync(FULL_MASK, s_wmax[lane]);
+            if (lane == 0) s_hot = m & (BPB - 1);
+        }
+        __syncthreads();
+        // place every key (keys again from their hashes); the fullest bucket's keys a warp at a time
+        const uint32_t jh = s_hot;
+#pragma unroll
+        for (int g = 0; g < GR; ++g) {
+            if ((uint32_t)g >= ng) break;
+            // the lanes of this warp that hold group g: those with tid + g * SB_THREADS < nv
+            const uint32_t first_v = g * SB_THREADS + w * 32;
+            const unsigned act = nv - first_v >= 32 ? FULL_MASK : (1u << (nv - first_v)) - 1u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = (jw[2 * g + u / 2] >> (16 * (u & 1))) & 0xffffu;
+                const unsigned hm = __ballot_sync(act, j == jh);
+                uint32_t pos = 0;
+                if (j == jh) {
+                    const int leader = __ffs(hm) - 1;
+                    uint32_t base = 0;
+                    if ((int)lane == leader) base = atomicAdd(s_cnt + jh, (uint32_t)__popc(hm));
+                    pos = __shfl_sync(hm, base, leader) + __popc(hm & lanemask_lt());
+                } else if (j != 0xffffu) {
+                    pos = atomicAdd(s_cnt + j, 1u);
+                }
+                if (j != 0xffffu) {
+                    if (pos < nn) out[pos] = unhash_key32(key[4 * g + u], H);
+                    else bad = true;
+                }
+            }
+        }
+        __syncthreads();
+        *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+        if (tid == 0) start_copy(b, m2);  // the chunk after next, into this buffer
+    }
+    if (bad) atomicOr(err, DEVERR_BOUNDS);
+    if (failed && tid == 0) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        for (int c = 0; c < 2; ++c) {
+            if (s_e[c] == ~0u || s_hi[c] - s_lo[c] > SB_CAP) continue;
+            uint32_t polls = 0;
+            while (!mbar_test_parity(&s_bar[c], (parity >> c) & 1u) && ++polls < SB_WAIT_LIMIT) {
+            }
+        }
+    }
+}
+
 size_t local_smem_bytes(size_t key_bytes, bool hv) {
     const size_t cap = LOCAL_STAGE_BYTES / (key_bytes + (hv ? 4 : 0));
     return (size_t)BPB * 4 + BPB / 8 + 2 * MAX_HOT * 4 + cap * (key_bytes + (hv ? 4 : 0));
@@ -1491,6 +1790,15 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     // first pass digit: bin >> 7 (two passes) or the bin itself (one pass, P <= 128)
     const uint32_t shift1 = two ? 7u : 0u;
     const uint32_t R1 = two ? P1 : P;
+    // 32-bit keys without values: bins of at most SB_CAP keys go to k_bin_small,
+    // larger ones (up to MAX_HUGE_SB of them) are cut into SB_CAP-key chunks for
+    // k_big_place; otherwise bins of more than HUGE_T_BUILD keys (up to MAX_HUGE)
+    // are cut into HUGE_CHUNK-key chunks for k_bin_local
+    const bool small_path = sizeof(K) == 4 && !hv;
+    const uint32_t huge_t = small_path ? SB_CAP : HUGE_T_BUILD;
+    const uint32_t huge_chunk = small_path ? SB_CAP : HUGE_CHUNK;
+    const uint32_t max_huge = small_path ? MAX_HUGE_SB : MAX_HUGE;
+    const size_t max_items = small_path ? (size_t)(n / SB_CAP) + max_huge + 1 : 0;
 
     // scratch (zeroed part first): bin_count[P] | huge_count | counters
     //   | cnt_a[nch_a][RADIX] | cnt_b[nch_b_max][RADIX] | bin_start[P+1] | work[P]
@@ -1499,7 +1807,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
     const size_t o_cnt = off; off += al((size_t)P * 4);
-    const size_t o_hcount = off; off += al((size_t)MAX_HUGE * BPB * 4);
+    const size_t o_hcount = off; off += al((size_t)max_huge * BPB * 4);
     const size_t o_ctr = off; off += al(64);
     const size_t zero_bytes = off;
     const size_t o_ca = off; off += al((size_t)nch_a * RADIX * 4);
@@ -1508,10 +1816,11 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     const size_t o_start = off; off += al((size_t)(P + 1) * 4);
     const size_t o_work = off; off += al((size_t)P * 4);
     const size_t o_seg = off; off += al((size_t)(P1 + 1) * 4);
-    const size_t o_hbin = off; off += al((size_t)MAX_HUGE * 4);
-    const size_t o_hcs = off; off += al((size_t)(MAX_HUGE + 1) * 4);
+    const size_t o_hbin = off; off += al((size_t)max_huge * 4);
+    const size_t o_hcs = off; off += al((size_t)(max_huge + 1) * 4);
     const size_t o_plan = off; off += al(sizeof(Plan));
-    const size_t o_hcur = off; off += al((size_t)MAX_HUGE * BPB * 4);
+    const size_t o_hcur = off; off += al((size_t)max_huge * BPB * 4);
+    const size_t o_items = off; off += al(max_items * sizeof(uint4));
     const size_t o_ka = off; off += al(two ? n * sizeof(K) : 0);
     const size_t o_va = off; off += al(two && hv ? n * 4 : 0);
     const size_t o_kb = off; off += al(n * sizeof(K));
@@ -1533,6 +1842,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     uint32_t* huge_cs = reinterpret_cast<uint32_t*>(base + o_hcs);
     Plan* plan = reinterpret_cast<Plan*>(base + o_plan);
     uint32_t* huge_cursor = reinterpret_cast<uint32_t*>(base + o_hcur);
+    uint4* item_meta = reinterpret_cast<uint4*>(base + o_items);
     K* ka = reinterpret_cast<K*>(base + o_ka);
     uint32_t* va = reinterpret_cast<uint32_t*>(base + o_va);
     K* kb = reinterpret_cast<K*>(base + o_kb);
@@ -1559,14 +1869,12 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     // 32-bit keys move through the passes as their hashes (k_pass32), so every
     // kernel after the first pass reads hashes
     constexpr bool HASHED = sizeof(K) == 4;
-    // 32-bit keys without values: bins of at most SB_CAP keys go to k_bin_small
-    const bool small_path = sizeof(K) == 4 && !hv;
     // 2. plan
     if (e == cudaSuccess) {
         const uint32_t big_t = small_path ? SB_CAP : (uint32_t)(LOCAL_STAGE_BYTES / (sizeof(K) + (hv ? 4 : 0)));
         launch_begin("part_plan", s);
-        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, n, big_t, HUGE_T_BUILD, bin_start, seg, work, huge_bin,
-                                       huge_cs, plan, t.offsets, B);
+        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, n, big_t, huge_t, huge_chunk, max_huge, bin_start, seg,
+                                       work, huge_bin, huge_cs, plan, t.offsets, B);
         launch_end("part_plan", s);
         e = cudaGetLastError();
     }
@@ -1628,8 +1936,8 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     }
     if (e == cudaSuccess) {
         launch_begin("huge_scan", s);
-        k_huge_scan<<<MAX_HUGE, 1024, 0, s>>>(bin_start, huge_bin, plan, huge_count, huge_cursor, t.offsets, B,
-                                              t.finder);
+        k_huge_scan<<<max_huge, 1024, 0, s>>>(bin_start, huge_bin, huge_cs, plan, huge_count, huge_cursor,
+                                              t.offsets, B, t.finder, small_path ? item_meta : nullptr);
         launch_end("huge_scan", s);
         e = cudaGetLastError();
     }
@@ -1664,6 +1972,19 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
             e = t.finder.map ? run(k_bin_small<true, true>) : run(k_bin_small<true, false>);
         else
             e = t.finder.map ? run(k_bin_small<false, true>) : run(k_bin_small<false, false>);
+    }
+    if (e == cudaSuccess && small_path) {
+        auto run = [&](auto kern) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB_SMEM);
+            if (r != cudaSuccess) return r;
+            launch_begin("bin_big", s);
+            kern<<<grid_for(kern, SB_THREADS, SB_SMEM), SB_THREADS, SB_SMEM, s>>>(
+                reinterpret_cast<const uint32_t*>(kb), t.H, item_meta, plan, huge_cursor, n,
+                static_cast<uint32_t*>(t.keys), t.err);
+            launch_end("bin_big", s);
+            return cudaGetLastError();
+        };
+        e = (t.H.mode == MODE_POW2 && t.B >= BPB) ? run(k_big_place<true>) : run(k_big_place<false>);
     }
     dev_free(mem, s);
     return e;
@@ -1740,7 +2061,7 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
         launch_begin("part_plan", s);
         // bins of many queries first in the probe's work list; the bins with the
         // most (huge bins) are cut into HUGE_CHUNK-query work items
-        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, nq, 1u << 16, HUGE_T, bin_start, seg,
+        k_part_plan<<<1, 1024, 0, s>>>(bin_count, P, P1, P2, nq, 1u << 16, HUGE_T, HUGE_CHUNK, MAX_HUGE, bin_start, seg,
                                        reinterpret_cast<uint32_t*>(base + o_work),
                                        reinterpret_cast<uint32_t*>(base + o_hbin),
                                        reinterpret_cast<uint32_t*>(base + o_hcs), plan, nullptr, B);
@@ -1803,20 +2124,24 @@ template <typename K>
 cudaError_t ungroup_counts_impl(const Table& t, const GroupedQueries* g, const uint32_t* cs, uint32_t* tmp,
                                 uint32_t* counts, cudaStream_t s) {
     const Plan* plan = static_cast<const Plan*>(g->plan);
-    if (g->two) {
+    uint32_t* gerr = g->err ? g->err : t.err;
+    // 32-bit queries were grouped by k_pass32, whose tiles k_pass_reverse32 undoes
+    auto reverse = [&](const uint32_t* from, uint32_t* to, const ChunkMap& cm, uint32_t nch_host, uint32_t grid,
+                       const uint32_t* dr, const uint2* lb) {
         launch_begin("q_reverse", s);
-        k_pass_reverse<K><<<g->nch_b_max, PASS_THREADS, 0, s>>>(cs, tmp, g->cm_b, 0u, plan, g->dr_b, g->lb_b,
-                                                               (g->err ? g->err : t.err));
+        if (sizeof(K) == 4)
+            k_pass_reverse32<<<grid, P32_THREADS, 0, s>>>(from, to, cm, nch_host, plan, dr, lb, gerr);
+        else
+            k_pass_reverse<K><<<grid, PASS_THREADS, 0, s>>>(from, to, cm, nch_host, plan, dr, lb, gerr);
         launch_end("q_reverse", s);
-        cudaError_t e = cudaGetLastError();
+        return cudaGetLastError();
+    };
+    if (g->two) {
+        cudaError_t e = reverse(cs, tmp, g->cm_b, 0u, g->nch_b_max, g->dr_b, g->lb_b);
         if (e != cudaSuccess) return e;
         cs = tmp;
     }
-    launch_begin("q_reverse", s);
-    k_pass_reverse<K><<<g->nch_a, PASS_THREADS, 0, s>>>(cs, counts, g->cm_a, g->nch_a, plan, g->dr_a, g->lb_a,
-                                                       (g->err ? g->err : t.err));
-    launch_end("q_reverse", s);
-    return cudaGetLastError();
+    return reverse(cs, counts, g->cm_a, g->nch_a, g->nch_a, g->dr_a, g->lb_a);
 }
 
 }  // namespace
