@@ -42,7 +42,7 @@ std::atomic<uint64_t> g_launches{0};
 // ---- per-kernel event timing (diagnostics) ----
 const char* const kKernelNames[] = {"hist", "scan", "scatter", "probe", "long_prep", "long", "gather",
                                     "long_gather", "walk_stats", "part_hist", "part_plan", "chunk_scan", "chunk_count", "part_scatter", "part_scatter2", "huge_count",
-                                    "huge_scan", "bin_build", "bin_small", "bin_big", "q_part_count", "q_partition", "q_partition2", "q_reverse", "batch", "probe_multi", "scatter_counts", "sort_buckets",
+                                    "huge_items", "huge_scan", "bin_build", "bin_small", "bin_big", "q_part_count", "q_partition", "q_partition2", "q_reverse", "batch", "probe_multi", "scatter_counts", "sort_buckets",
                                     "sum_find", "sum_plan", "sum_count", "sum_finish", "probe_hash"};
 struct ProfRecord {
     const char* name;

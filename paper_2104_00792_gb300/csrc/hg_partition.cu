@@ -991,26 +991,30 @@ k_huge_count(const K* __restrict__ in, Hasher H, const uint32_t* __restrict__ bi
     }
 }
 
-// Huge bins, step 2: one CTA per huge bin scans its counts into offsets and
-// cursors; with item_meta, it also lists its work items as (bin slot e, bin p,
-// first key, end key).
+// The huge bins' work items as (bin slot e, bin p, first key, end key), one CTA per huge bin.
+__global__ void __launch_bounds__(256)
+k_huge_items(const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ huge_bin,
+             const uint32_t* __restrict__ huge_chunk_start, const Plan* __restrict__ plan, uint4* item_meta) {
+    const uint32_t e = blockIdx.x;
+    if (e >= plan->n_huge) return;
+    const uint32_t p = huge_bin[e];
+    const uint32_t chunk = plan->huge_chunk, bs = bin_start[p], be = bin_start[p + 1];
+    const uint32_t i0 = huge_chunk_start[e], ni = huge_chunk_start[e + 1] - i0;
+    for (uint32_t k = threadIdx.x; k < ni; k += blockDim.x) {
+        const uint32_t lo = bs + k * chunk;
+        item_meta[i0 + k] = make_uint4(e, p, lo, min(be, lo + chunk));
+    }
+}
+
+// Huge bins, step 2: one CTA per huge bin scans its counts into offsets and cursors.
 __global__ void __launch_bounds__(1024)
 k_huge_scan(const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ huge_bin,
-            const uint32_t* __restrict__ huge_chunk_start, const Plan* __restrict__ plan,
-            const uint32_t* __restrict__ huge_count, uint32_t* huge_cursor, uint32_t* offsets, uint64_t B,
-            LongFinder LF, uint4* item_meta) {
+            const Plan* __restrict__ plan, const uint32_t* __restrict__ huge_count, uint32_t* huge_cursor,
+            uint32_t* offsets, uint64_t B, LongFinder LF) {
     __shared__ uint32_t s_warp[33];
     const uint32_t e = blockIdx.x;
     if (e >= plan->n_huge) return;
     const uint32_t p = huge_bin[e];
-    if (item_meta) {
-        const uint32_t chunk = plan->huge_chunk, bs = bin_start[p], be = bin_start[p + 1];
-        const uint32_t i0 = huge_chunk_start[e], ni = huge_chunk_start[e + 1] - i0;
-        for (uint32_t k = threadIdx.x; k < ni; k += blockDim.x) {
-            const uint32_t lo = bs + k * chunk;
-            item_meta[i0 + k] = make_uint4(e, p, lo, min(be, lo + chunk));
-        }
-    }
     const uint64_t b0 = (uint64_t)p << BIN_SHIFT;
     const uint32_t nb = (uint32_t)min((uint64_t)BPB, B - b0);
     uint32_t running = bin_start[p], tot;
@@ -1557,6 +1561,114 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
 // atomic, and their keys go out as consecutive words.
 constexpr uint32_t MAX_HUGE_SB = 1536;  // bins of more than SB_CAP keys with a counter/cursor slice
 
+// Step 1 for the chunks of k_big_place: each chunk's bucket histogram (shared
+// memory), added into its bin's global counts; chunks arrive as in k_big_place.
+template <bool POW2>
+__global__ void __launch_bounds__(SB_THREADS, 1)
+k_big_count(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__ item_meta,
+            const Plan* __restrict__ plan, uint32_t* __restrict__ huge_count, uint32_t* err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* const s_buf0 = s_cnt + BPB;  // buffer b at s_buf0 + b * SB_BUF_KEYS
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_e[2], s_p[2], s_lo[2], s_hi[2];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t items = plan->huge_chunks;
+    const uint32_t G = gridDim.x;
+    auto start_copy = [&](int b, uint4 m) {
+        const uint32_t e = m.x, p = m.y, lo = m.z, hi = m.w;
+        s_e[b] = e;
+        s_p[b] = p;
+        s_lo[b] = lo;
+        s_hi[b] = hi;
+        if (e == ~0u || hi - lo > SB_CAP) return;
+        const uint32_t klo = lo & ~3u, khi = (hi + 3) & ~3u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar[b], (khi - klo) * 4);
+        if (khi > klo) bulk_load(s_buf0 + b * SB_BUF_KEYS, in + klo, (khi - klo) * 4, &s_bar[b]);
+    };
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const uint4 none = make_uint4(~0u, 0, 0, 0);
+        start_copy(0, blockIdx.x < items ? item_meta[blockIdx.x] : none);
+        start_copy(1, blockIdx.x + G < items ? item_meta[blockIdx.x + G] : none);
+    }
+    *reinterpret_cast<uint4*>(s_cnt + 8 * tid) = make_uint4(0, 0, 0, 0);
+    *reinterpret_cast<uint4*>(s_cnt + 8 * tid + 4) = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    uint32_t parity = 0;
+    bool failed = false, bad = false;
+    int b = 0;
+    for (uint32_t it = blockIdx.x; it < items; it += G, b ^= 1) {
+        const uint32_t e = s_e[b], p = s_p[b], s0 = s_lo[b], s1 = s_hi[b];
+        uint4 m2 = make_uint4(~0u, 0, 0, 0);
+        if (tid == 0 && it + 2 * G < items) m2 = item_meta[it + 2 * G];
+        const bool ok = e != ~0u && s1 - s0 <= SB_CAP;
+        bad |= !ok;
+        if (ok) {
+            uint32_t polls = 0;
+            while (!mbar_test_parity(&s_bar[b], (parity >> b) & 1u) && ++polls < SB_WAIT_LIMIT) {
+            }
+            failed = polls >= SB_WAIT_LIMIT;
+            parity ^= 1u << b;
+        }
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        const uint32_t nk = ok ? s1 - s0 : 0u;
+        const uint32_t klo = s0 & ~3u, a = s0 - klo, nv = (a + nk + 3) / 4;
+        const uint32_t* buf = s_buf0 + b * SB_BUF_KEYS;
+        const uint32_t b0 = p << BIN_SHIFT;
+        const uint32_t nb = POW2 ? BPB : (uint32_t)min((uint64_t)BPB, H.B - b0);
+        for (uint32_t v = tid; v < nv; v += SB_THREADS) {
+            const uint4 x = reinterpret_cast<const uint4*>(buf)[v];
+            const uint32_t hw[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (4 * v + u - a < nk) {
+                    uint32_t j;
+                    if (POW2) {
+                        j = hw[u] & (BPB - 1);
+                    } else {
+                        j = bucket_of_hash(hw[u], H) - b0;
+                        bad |= j >= nb;
+                        j = min(j, nb - 1);
+                    }
+                    atomicAdd(s_cnt + j, 1u);
+                }
+            }
+        }
+        __syncthreads();
+        // flush: thread t adds its 8 buckets' nonzero counts into the bin's, and clears them
+        const uint32_t j0 = 8 * tid;
+        {
+            const uint4 c0 = *reinterpret_cast<const uint4*>(s_cnt + j0);
+            const uint4 c1 = *reinterpret_cast<const uint4*>(s_cnt + j0 + 4);
+            const uint32_t cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (cv[u]) atomicAdd(huge_count + (uint64_t)e * BPB + j0 + u, cv[u]);
+            *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(0, 0, 0, 0);
+        }
+        __syncthreads();
+        if (tid == 0) start_copy(b, m2);
+    }
+    if (bad) atomicOr(err, DEVERR_BOUNDS);
+    if (failed && tid == 0) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        for (int c = 0; c < 2; ++c) {
+            if (s_e[c] == ~0u || s_hi[c] - s_lo[c] > SB_CAP) continue;
+            uint32_t polls = 0;
+            while (!mbar_test_parity(&s_bar[c], (parity >> c) & 1u) && ++polls < SB_WAIT_LIMIT) {
+            }
+        }
+    }
+}
+
 template <bool POW2>
 __global__ void __launch_bounds__(SB_THREADS, 1)
 k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__ item_meta,
@@ -1922,7 +2034,24 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
         }
     }
     // 4. huge bins: chunk histograms, then their offsets and cursors
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && small_path) {
+        // the chunks as (bin slot, bin, first key, end key), then their counts by TMA-fed CTAs
+        launch_begin("huge_items", s);
+        k_huge_items<<<max_huge, 256, 0, s>>>(bin_start, huge_bin, huge_cs, plan, item_meta);
+        launch_end("huge_items", s);
+        e = cudaGetLastError();
+        auto run = [&](auto kern) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB_SMEM);
+            if (r != cudaSuccess) return r;
+            launch_begin("huge_count", s);
+            kern<<<grid_for(kern, SB_THREADS, SB_SMEM), SB_THREADS, SB_SMEM, s>>>(
+                reinterpret_cast<const uint32_t*>(kb), t.H, item_meta, plan, huge_count, t.err);
+            launch_end("huge_count", s);
+            return cudaGetLastError();
+        };
+        if (e == cudaSuccess)
+            e = (t.H.mode == MODE_POW2 && t.B >= BPB) ? run(k_big_count<true>) : run(k_big_count<false>);
+    } else if (e == cudaSuccess) {
         auto kern = k_huge_count<K, HASHED>;
         const size_t smem = (size_t)BPB * 4;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1936,8 +2065,8 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     }
     if (e == cudaSuccess) {
         launch_begin("huge_scan", s);
-        k_huge_scan<<<max_huge, 1024, 0, s>>>(bin_start, huge_bin, huge_cs, plan, huge_count, huge_cursor,
-                                              t.offsets, B, t.finder, small_path ? item_meta : nullptr);
+        k_huge_scan<<<max_huge, 1024, 0, s>>>(bin_start, huge_bin, plan, huge_count, huge_cursor, t.offsets, B,
+                                              t.finder);
         launch_end("huge_scan", s);
         e = cudaGetLastError();
     }
