@@ -597,13 +597,13 @@ k_pass32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ in_v, uin
     const uint32_t end = a + (uint32_t)(hi64 - lo64);
     const uint32_t* __restrict__ inc = in + (lo64 - a);
     const uint32_t* __restrict__ inc_v = PM == 1 ? in_v + (lo64 - a) : nullptr;
-    uint32_t* __restrict__ drc = DR ? dr_out + (lo64 - a) : nullptr;
+    uint16_t* __restrict__ drc = DR ? reinterpret_cast<uint16_t*>(dr_out) + (lo64 - a) : nullptr;
     uint2* __restrict__ lbc = DR ? tile_lb + (uint64_t)c * TILES_PER_CHUNK * RADIX : nullptr;
     const uint32_t base32 = (uint32_t)(lo64 - a);  // (index payloads: positions fit 32 bits)
     const bool vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0 &&
                      (PM != 1 || (reinterpret_cast<uintptr_t>(in_v) & 15) == 0);
     const uint32_t vend = in_padded ? end + 3 : end;  // groups wholly below vend are read as vectors
-    const bool dr_vec = DR && (reinterpret_cast<uintptr_t>(dr_out) & 15) == 0;
+    const bool dr_vec = DR && (reinterpret_cast<uintptr_t>(dr_out) & 7) == 0;
     for (uint32_t d = tid; d < RADIX; d += P32_THREADS) {
         s_cnt[d] = 0;
         s_run[d] = d < R ? chunk_base[(uint64_t)c * RADIX + d] : 0u;
@@ -683,24 +683,27 @@ k_pass32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ in_v, uin
             s_cnt[d] = 0;
         }
         __syncthreads();
-        if (DR) {
-            if (FULL && dr_vec) {
-#pragma unroll
-                for (int g = 0; g < NG; ++g)
-                    *reinterpret_cast<uint4*>(drc + t0 + (tid + g * P32_THREADS) * 4) =
-                        make_uint4(dr[4 * g], dr[4 * g + 1], dr[4 * g + 2], dr[4 * g + 3]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < IPT; ++j)
-                    if (dr[j] != 0xffffffffu) drc[t0 + (tid + (j / 4) * P32_THREADS) * 4 + (j % 4)] = dr[j];
-            }
-        }
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             if (FULL || dr[j] != 0xffffffffu) {
                 const uint32_t pos = s_lb[dr[j] & 0xffu].x + (dr[j] >> 8);
                 s_h[pos] = w[j];
                 if (PM) s_pay[pos] = v[j];
+                if (DR) dr[j] = pos;
+            }
+        }
+        // DR: each element's record is its staging position in the tile (16 bits):
+        // the reverse pass finds every staged word's source from the tile's runs
+        if (DR) {
+            if (FULL && dr_vec) {
+#pragma unroll
+                for (int g = 0; g < NG; ++g)
+                    *reinterpret_cast<uint2*>(drc + t0 + (tid + g * P32_THREADS) * 4) =
+                        make_uint2(dr[4 * g] | (dr[4 * g + 1] << 16), dr[4 * g + 2] | (dr[4 * g + 3] << 16));
+            } else {
+#pragma unroll
+                for (int j = 0; j < IPT; ++j)
+                    if (dr[j] != 0xffffffffu) drc[t0 + (tid + (j / 4) * P32_THREADS) * 4 + (j % 4)] = (uint16_t)dr[j];
             }
         }
         __syncthreads();
@@ -827,10 +830,14 @@ k_pass_reverse(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, Chu
     }
 }
 
-// k_pass_reverse for the 32-bit passes (k_pass32): 256 threads, each holding
-// 32 elements of a tile as eight 4-element groups (element x of the chunk's
-// window in thread (x / 4) % 256, as in the forward pass), so the records come
-// in and the values go out 16 bytes at a time.
+// k_pass_reverse for the 32-bit passes (k_pass32), whose records are each
+// element's 16-bit staging position in its tile.  Every warp copies whole runs
+// of the tile (digit d's run: staged positions [loc_d, loc_{d+1}) from
+// base_d + ...) into shared memory with asynchronous copies, then each element
+// takes its value from its staging position.  256 threads, each holding 32
+// elements of a tile as eight 4-element groups (element x of the chunk's window
+// in thread (x / 4) % 256, as in the forward pass), so the records come in 8
+// bytes and the values go out 16 bytes at a time.
 __global__ void __launch_bounds__(P32_THREADS, 3)
 k_pass_reverse32(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, ChunkMap cm, uint32_t nch_host,
                  const Plan* __restrict__ plan, const uint32_t* __restrict__ dr_in, const uint2* __restrict__ tile_lb,
@@ -839,9 +846,8 @@ k_pass_reverse32(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, C
     constexpr int NG = P32<0>::IPT / 4;
     constexpr int PER = P32<0>::IPT;
     __shared__ __align__(16) uint32_t s_val[TILE];
-    __shared__ uint8_t s_dig[TILE];
-    __shared__ uint2 s_lb[RADIX];
-    const uint32_t tid = threadIdx.x;
+    __shared__ uint2 s_lb[RADIX + 1];
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
     const uint32_t c = blockIdx.x;
     if (c >= nch) return;
@@ -852,25 +858,30 @@ k_pass_reverse32(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, C
     // lo - a + x, valid for a <= x < end
     const uint32_t a = (uint32_t)(lo & 3);
     const uint32_t end = a + (uint32_t)(hi - lo);
-    const uint32_t* __restrict__ drc = dr_in + (lo - a);  // (records: an internal array, padded and aligned)
+    // (records: an internal array, 8-byte aligned and padded past its end)
+    const uint16_t* __restrict__ drc = reinterpret_cast<const uint16_t*>(dr_in) + (lo - a);
     uint32_t* __restrict__ dstc = dst + (lo - a);
     const bool dvec = (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
     const uint2* __restrict__ lbc = tile_lb + (uint64_t)c * TILES_PER_CHUNK * RADIX;
-    uint32_t drs[PER];
+    uint32_t pj[PER / 2];  // two 16-bit staging positions per word, 0xffff = no element
     uint2 lbr = make_uint2(0, 0);
     auto fetch = [&](uint32_t t0) {
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
             const uint32_t x0 = t0 + (tid + g * P32_THREADS) * 4;
+            uint2 q = make_uint2(0xffffffffu, 0xffffffffu);
             if (x0 < end) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4*>(drc + x0));
-                drs[4 * g] = x0 >= a ? q.x : 0xffffffffu;
-                drs[4 * g + 1] = x0 + 1 >= a && x0 + 1 < end ? q.y : 0xffffffffu;
-                drs[4 * g + 2] = x0 + 2 >= a && x0 + 2 < end ? q.z : 0xffffffffu;
-                drs[4 * g + 3] = x0 + 3 < end ? q.w : 0xffffffffu;
-            } else {
-                drs[4 * g] = drs[4 * g + 1] = drs[4 * g + 2] = drs[4 * g + 3] = 0xffffffffu;
+                q = __ldg(reinterpret_cast<const uint2*>(drc + x0));
+                if (x0 < a || x0 + 4 > end) {  // a window edge: mark the elements outside the chunk
+                    uint32_t m[4] = {q.x & 0xffffu, q.x >> 16, q.y & 0xffffu, q.y >> 16};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (x0 + u < a || x0 + u >= end) m[u] = 0xffffu;
+                    q = make_uint2(m[0] | (m[1] << 16), m[2] | (m[3] << 16));
+                }
             }
+            pj[2 * g] = q.x;
+            pj[2 * g + 1] = q.y;
         }
         if (tid < RADIX) lbr = __ldg(lbc + (t0 / TILE) * RADIX + tid);
     };
@@ -878,47 +889,37 @@ k_pass_reverse32(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, C
     for (uint32_t t0 = 0; t0 < end; t0 += TILE) {
         const uint32_t cnt_tile = min(end, t0 + (uint32_t)TILE) - max(a, t0);  // valid elements
         if (tid < RADIX) s_lb[tid] = lbr;
+        if (tid == 0) s_lb[RADIX] = make_uint2(cnt_tile, 0);
         __syncthreads();
-        // every element marks its staging position with its digit ...
-        static_assert(TILE < 0xffff, "staging positions are kept in 16 bits");
-        uint32_t pj[PER / 2];  // two 16-bit staging positions per word, 0xffff = none
+        // the tile's runs, a warp per digit (d = warp, warp + 8, ...), copied to
+        // their staging positions
+        for (uint32_t d = warp; d < RADIX; d += P32_THREADS / 32) {
+            const uint2 lb = s_lb[d];
+            const uint32_t len = min(s_lb[d + 1].x, (uint32_t)TILE) - min(lb.x, (uint32_t)TILE);
+            for (uint32_t k = lane; k < len; k += 32) cp_async4(s_val + lb.x + k, src + lb.y + k);
+        }
+        uint32_t pos_now[PER / 2];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            uint32_t pos = 0xffffu;
-            if (drs[j] != 0xffffffffu) {
-                const uint32_t p = s_lb[drs[j] & 0xffu].x + (drs[j] >> 8);
-                if (p < (uint32_t)TILE) {
-                    s_dig[p] = (uint8_t)(drs[j] & 0xffu);
-                    pos = p;
-                } else {
-                    atomicOr(err, DEVERR_BOUNDS);
-                }
-            }
-            if (j & 1) pj[j / 2] |= pos << 16;
-            else pj[j / 2] = pos;
-        }
-        __syncthreads();
-        // ... so that the tile's runs are read back contiguously in staging order
-        // (asynchronous copies straight into shared memory)
-        for (uint32_t i = tid; i < cnt_tile; i += P32_THREADS) {
-            const uint2 lb = s_lb[s_dig[i]];
-            cp_async4(s_val + i, src + lb.y + (i - lb.x));
-        }
+        for (int q = 0; q < PER / 2; ++q) pos_now[q] = pj[q];
         const uint32_t t1 = t0 + TILE;
         if (t1 < end) fetch(t1);
         cp_async_wait_all();
         __syncthreads();
-        // s_lb and s_dig are not read past this point, and s_val is next written
-        // after the next tile's second barrier, so no barrier ends the tile
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
             const uint32_t x0 = t0 + (tid + g * P32_THREADS) * 4;
             uint32_t pos[4], val[4];
+            pos[0] = pos_now[2 * g] & 0xffffu;
+            pos[1] = pos_now[2 * g] >> 16;
+            pos[2] = pos_now[2 * g + 1] & 0xffffu;
+            pos[3] = pos_now[2 * g + 1] >> 16;
+            bool bad = false;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                pos[u] = (pj[(4 * g + u) / 2] >> (((4 * g + u) & 1) * 16)) & 0xffffu;
-                val[u] = pos[u] != 0xffffu ? s_val[pos[u]] : 0u;
+                bad |= pos[u] != 0xffffu && pos[u] >= cnt_tile;
+                val[u] = pos[u] < cnt_tile ? s_val[pos[u]] : 0u;
             }
+            if (bad) atomicOr(err, DEVERR_BOUNDS);
             if (dvec && pos[0] != 0xffffu && pos[3] != 0xffffu) {
                 *reinterpret_cast<uint4*>(dstc + x0) = make_uint4(val[0], val[1], val[2], val[3]);
             } else {
@@ -927,6 +928,8 @@ k_pass_reverse32(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, C
                     if (pos[u] != 0xffffu) dstc[x0 + u] = val[u];
             }
         }
+        // s_val is rewritten by the next tile's copies only after its first barrier
+        __syncthreads();
     }
 }
 
@@ -2148,8 +2151,10 @@ cudaError_t group_queries_impl(const Table& t, const K* q, uint64_t nq, GroupedQ
     const size_t o_plan = off; off += al(sizeof(Plan));
     const size_t o_lba = off; off += al((size_t)nch_a * TILES_PER_CHUNK * RADIX * 8);
     const size_t o_lbb = off; off += al(two ? (size_t)nch_b_max * TILES_PER_CHUNK * RADIX * 8 : 0);
-    const size_t o_dra = off; off += al(nq * 4);
-    const size_t o_drb = off; off += al(two ? nq * 4 : 0);
+    // reverse-pass records: 32-bit queries 16-bit staging positions, else (rank, digit) words
+    const size_t rec_bytes = sizeof(K) == 4 ? 2 : 4;
+    const size_t o_dra = off; off += al(nq * rec_bytes + 16);
+    const size_t o_drb = off; off += al(two ? nq * rec_bytes + 16 : 0);
     const size_t o_qa = off; off += al(two ? nq * sizeof(K) : 0);
     const size_t o_qb = off; off += al((nq + 4) * sizeof(K));
     cudaError_t e = dev_alloc(&g->mem, off, s);
