@@ -727,7 +727,9 @@ k_pass32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ in_v, uin
         } else {
             for (uint32_t i = tid; i < cnt_tile; i += P32_THREADS) put(i);
         }
-        __syncthreads();
+        // no barrier ends the tile: the next tile's ranking touches only s_cnt,
+        // and s_lb and s_h are rewritten only after its first barrier, which
+        // every thread reaches after this write-out
     };
     __syncthreads();
     if (end > a) load(0, is_full(0));
@@ -928,8 +930,9 @@ k_pass_reverse32(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, C
                     if (pos[u] != 0xffffu) dstc[x0 + u] = val[u];
             }
         }
-        // s_val is rewritten by the next tile's copies only after its first barrier
-        __syncthreads();
+        // no barrier ends the tile: s_val is rewritten by the next tile's copies
+        // only after its first barrier, which every thread reaches after this
+        // tile's reads (s_lb, rewritten before that barrier, is not read here)
     }
 }
 
