@@ -537,8 +537,8 @@ def run_ours(args, rank, world, local_rank):
         "part_scatter2": 2 * k * N,                   # the second (per coarse segment)
         "bin_build": 2 * k * N + o * (B + 1),         # per-bin counting sort: keys in, keys + offsets out
         "q_part_count": k * Q,
-        "q_partition": 2 * k * Q + 4 * Q,             # queries grouped + their positions
-        "q_partition2": 2 * k * Q + 4 * Q,
+        "q_partition": 2 * k * Q + 2 * Q,             # queries grouped + their 16-bit staging positions
+        "q_partition2": 2 * k * Q + 2 * Q,
         "probe": k * Q + 8 * Q + k * (W - WL) + 4 * Q,   # direct probe (tables that stay in L2)
         "long": k * WL,
     }
@@ -547,7 +547,7 @@ def run_ours(args, rank, world, local_rank):
         # each bin's offsets and keys once (into shared memory) and writes the counts
         model["probe"] = k * Q + 4 * (B + 1) + k * N + 4 * Q
         model["chunk_count"] = k * N                   # (same for the query side: Q = N here)
-        model["q_reverse"] = 12 * Q                    # ranks, grouped counts in, counts out
+        model["q_reverse"] = 10 * Q                    # positions, grouped counts in, counts out
     # the method's own byte model for the whole step (build + probe; offsets 4 B)
     if flags:
         # summarised long buckets (HG_LONG_SUMMARY): each of their queries reads the
@@ -581,7 +581,29 @@ def run_ours(args, rank, world, local_rank):
     tot = sum(v["ms_per_launch"] * v["launches"] for v in per_kernel.values()) or 1.0
     for v in per_kernel.values():
         v["share"] = v["ms_per_launch"] * v["launches"] / tot
-    traffic_total, traffic_note = step_traffic(per_kernel, args.steps)
+    # stages whose kernels split one piece of the method's work on the device, so
+    # that only their sum has a byte model: the bin build (k_bin_small takes the
+    # small bins, k_big_place the chunks of the large ones after counting them)
+    # and the grouped probe (the hash join, the walking probe for the bins it
+    # leaves, and the long-bucket walks)
+    stages = {"bin_stage": (("bin_small", "bin_big", "huge_count", "huge_scan", "huge_items", "bin_build"),
+                            2 * k * N + o * (B + 1)),
+              "probe_stage": (("probe_hash", "probe", "long_prep", "long"), k * Q + k * N + 4 * Q)}
+    for sname, (parts, sbytes) in stages.items():
+        got = [per_kernel[p] for p in parts if p in per_kernel]
+        if sname == "probe_stage" and "probe_hash" not in per_kernel:
+            continue  # (no grouped probe: the direct probe has its own model)
+        if got:
+            steps_ms = sum(v["ms_per_launch"] * v["launches"] for v in got) / args.steps
+            per_kernel[sname] = {"launches": args.steps, "ms_per_launch": steps_ms, "share": None,
+                                 "model_bytes": sbytes, "parts": [p for p in parts if p in per_kernel]}
+            model[sname] = sbytes
+            for p in parts:
+                model.pop(p, None)
+    tot_k = sum(v["ms_per_launch"] * v["launches"] for n, v in per_kernel.items() if "parts" not in v) or 1.0
+    for v in per_kernel.values():
+        v["share"] = v["ms_per_launch"] * v["launches"] / tot_k
+    traffic_total, traffic_note = step_traffic({n: v for n, v in per_kernel.items() if "parts" not in v}, args.steps)
     dom = max((n for n in per_kernel if n in model), key=lambda n: per_kernel[n]["share"])
     d = per_kernel[dom]
     achieved = model[dom] / (d["ms_per_launch"] * 1e-3) / 1e9
