@@ -11,17 +11,22 @@
 //                    the second pass's chunks, the huge bins, the work list.
 //   3. MSD partition by bin in one or two passes of radix <= 128, each a
 //      reduce-then-scan: per-chunk digit counts -> k_chunk_scan (where each
-//      chunk's run of each digit starts) -> k_pass_down, where one CTA walks
+//      chunk's run of each digit starts) -> the downsweep, where one CTA walks
 //      its chunk tile by tile, ranks keys per digit in shared memory, stages
 //      them in digit order and writes each digit's run contiguously.  No CTA
-//      ever waits for another.
-//   4. k_bin_local   per bin: counting sort by bucket in shared memory
-//                    (histogram, exclusive scan -> the bin's offsets,
-//                    placement), staged so the output is written in
-//                    contiguous runs.  When a bin does not fit, its largest
-//                    buckets go straight to global memory (their keys land on
-//                    consecutive positions) and the rest is staged.
-//      Bins above HUGE_T_BUILD keys are split over many CTAs: k_huge_count ->
+//      ever waits for another.  32-bit keys move as their hashes (k_pass32;
+//      fmix32 is a bijection, so later stages read buckets straight from the
+//      words and recover keys with fmix32_inv); 64-bit keys move as keys
+//      (k_pass_down).
+//   4. Per-bin counting sort by bucket (Algorithm 1 inside one bin):
+//      32-bit keys without values: bins of at most SB_CAP keys by k_bin_small
+//      (one bulk copy per bin into shared memory, keys held in registers),
+//      larger bins cut into SB_CAP-key chunks: k_big_count (chunk bucket
+//      histograms) -> k_huge_scan (offsets and per-bucket cursors) ->
+//      k_big_place (one global atomic per nonempty bucket per chunk).
+//      Otherwise k_bin_local (staged in shared memory; when a bin does not
+//      fit, its largest buckets go straight to global memory), with bins
+//      above HUGE_T_BUILD keys split over many CTAs: k_huge_count ->
 //      k_huge_scan -> chunk placement through per-bucket cursors.
 // The result equals the direct build's (offsets bit-exact; the order inside
 // a bucket differs, which Algorithm 1 leaves free).
@@ -558,6 +563,7 @@ k_pass_down(const K* __restrict__ in, const uint32_t* __restrict__ in_v, uint64_
 // amortised over more keys.  Element li of a tile is held by thread
 // (li / 4) % 256, slot (li / 1024) * 4 + li % 4.
 constexpr int P32_THREADS = 256;
+constexpr uint32_t P32_COPIES = 4;  // counters per digit (the code reads them as one uint4)
 template <int PM>
 struct P32 {
     static constexpr int IPT = PM ? 16 : 32;
@@ -579,9 +585,15 @@ k_pass32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ in_v, uin
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);  // staged words [TILE]
     uint32_t* s_pay = s_h + TILE;                       // staged payloads [TILE] (PM)
-    __shared__ uint32_t s_cnt[RADIX], s_run[RADIX], s_warp[4];
+    // each digit's count is kept in P32_COPIES counters, lane l adding to copy
+    // l % P32_COPIES, so the lanes of a warp whose keys share a digit (duplicated
+    // keys) wait on at most 32 / P32_COPIES increments of one word; s_sub: where
+    // each copy's keys start in the staged tile
+    __shared__ __align__(16) uint32_t s_cnt[RADIX * P32_COPIES], s_sub[RADIX * P32_COPIES];
+    __shared__ uint32_t s_run[RADIX], s_warp[4];
     __shared__ uint2 s_lb[RADIX];  // (offset of the digit's run inside the tile, its destination)
     const uint32_t tid = threadIdx.x;
+    const uint32_t cp = lane_id() & (P32_COPIES - 1);
     const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
     const uint32_t c = blockIdx.x;
     if (c >= nch) return;
@@ -604,10 +616,8 @@ k_pass32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ in_v, uin
                      (PM != 1 || (reinterpret_cast<uintptr_t>(in_v) & 15) == 0);
     const uint32_t vend = in_padded ? end + 3 : end;  // groups wholly below vend are read as vectors
     const bool dr_vec = DR && (reinterpret_cast<uintptr_t>(dr_out) & 7) == 0;
-    for (uint32_t d = tid; d < RADIX; d += P32_THREADS) {
-        s_cnt[d] = 0;
-        s_run[d] = d < R ? chunk_base[(uint64_t)c * RADIX + d] : 0u;
-    }
+    for (uint32_t d = tid; d < RADIX * P32_COPIES; d += P32_THREADS) s_cnt[d] = 0;
+    for (uint32_t d = tid; d < RADIX; d += P32_THREADS) s_run[d] = d < R ? chunk_base[(uint64_t)c * RADIX + d] : 0u;
     // the digit is masked to the radix, so shared-memory indices stay in bounds
     // whatever the word; a consistent plan never needs the mask.  POW2: B = 2^k,
     // the bucket is the hash's low k bits
@@ -664,13 +674,14 @@ k_pass32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ in_v, uin
             const uint32_t d = digit(w[j]);
             const uint32_t x = t0 + (tid + (j / 4) * P32_THREADS) * 4 + (j % 4);
             const bool ok = FULL || (x >= a && x < end);
-            dr[j] = ok ? ((atomicAdd(s_cnt + d, 1u) << 8) | d) : 0xffffffffu;
+            dr[j] = ok ? ((atomicAdd(s_cnt + d * P32_COPIES + cp, 1u) << 8) | d) : 0xffffffffu;
         }
         __syncthreads();
         // digit offsets inside the tile (first 4 warps), and where each run goes
         if (tid < RADIX) {
             const uint32_t d = tid;
-            const uint32_t cd = s_cnt[d];
+            const uint4 c4 = *reinterpret_cast<const uint4*>(s_cnt + d * P32_COPIES);
+            const uint32_t cd = c4.x + c4.y + c4.z + c4.w;
             const uint32_t incl = warp_inclusive_scan(cd);
             if (lane_id() == 31) s_warp[d >> 5] = incl;
             asm volatile("bar.sync 1, 128;");
@@ -678,15 +689,17 @@ k_pass32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ in_v, uin
             for (uint32_t x = 0; x < (d >> 5); ++x) wp += s_warp[x];
             const uint2 lb = make_uint2(wp + incl - cd, s_run[d]);
             s_lb[d] = lb;
+            *reinterpret_cast<uint4*>(s_sub + d * P32_COPIES) =
+                make_uint4(lb.x, lb.x + c4.x, lb.x + c4.x + c4.y, lb.x + c4.x + c4.y + c4.z);
             if (DR) lbc[(t0 / TILE) * RADIX + d] = lb;
             s_run[d] += cd;
-            s_cnt[d] = 0;
+            *reinterpret_cast<uint4*>(s_cnt + d * P32_COPIES) = make_uint4(0, 0, 0, 0);
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             if (FULL || dr[j] != 0xffffffffu) {
-                const uint32_t pos = s_lb[dr[j] & 0xffu].x + (dr[j] >> 8);
+                const uint32_t pos = s_sub[(dr[j] & 0xffu) * P32_COPIES + cp] + (dr[j] >> 8);
                 s_h[pos] = w[j];
                 if (PM) s_pay[pos] = v[j];
                 if (DR) dr[j] = pos;
@@ -1420,13 +1433,14 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
         uint32_t* buf = s_buf0 + b * SB_BUF_KEYS;
         const uint32_t b0 = p << BIN_SHIFT;
         const uint32_t nb = POW2 ? BPB : (uint32_t)min((uint64_t)BPB, H.B - b0);
-        // histogram.  Thread t reads 16-byte groups t, t + 1024, ...; the bucket
-        // inside the bin of each key (13 bits; 0xffff = not a key of the bin) is
-        // kept in registers for the placement, two per word.
+        // histogram.  Thread t reads 16-byte groups t, t + 1024, ...; each key's
+        // rank among the bin's keys of its bucket is the value its histogram
+        // increment returns, kept in registers for the placement, two per word
+        // (16 bits each: ranks are below SB_CAP; 0xffff = not a key of the bin).
         // (groups past the thread's last are skipped by a branch, which is the
         // same for all lanes of a warp but the last one: no predicated-off work)
         const uint32_t ng = nv > tid ? (nv - tid + SB_THREADS - 1) / SB_THREADS : 0u;
-        uint32_t key[SB_KPT], jw[2 * GR];
+        uint32_t key[SB_KPT], rk[2 * GR];
 #pragma unroll
         for (int g = 0; g < GR; ++g) {
             if ((uint32_t)g >= ng) break;
@@ -1452,11 +1466,10 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
                         bad |= in_bin && j >= nb;
                         j = min(j, nb - 1);
                     }
-                    if (in_bin) atomicAdd(s_cnt + j, 1u);
-                    js[e] = in_bin ? j : 0xffffu;
+                    js[e] = in_bin ? atomicAdd(s_cnt + j, 1u) : 0xffffu;
                 }
-                jw[2 * g] = js[0] | (js[1] << 16);
-                jw[2 * g + 1] = js[2] | (js[3] << 16);
+                rk[2 * g] = js[0] | (js[1] << 16);
+                rk[2 * g + 1] = js[2] | (js[3] << 16);
             }
         }
         if (tid == 0 && p2 != ~0u) {
@@ -1500,21 +1513,25 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
             for (int e = 0; e < 8; ++e)
                 if (cv[e] > SUM_MIN_LEN) note_long(LF, b0 + j0 + e);
         }
-        // placement cursors, as buffer indices
+        // bucket starts, as buffer indices
         *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(a + st[0], a + st[1], a + st[2], a + st[3]);
         *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(a + st[4], a + st[5], a + st[6], a + st[7]);
         __syncthreads();
-        // placement into the same buffer (every word is in registers now)
+        // placement into the same buffer (every word is in registers now): the
+        // bucket's start plus the key's rank, no atomics; the bucket comes again
+        // from the word (POW2: its low bits)
 #pragma unroll
         for (int g = 0; g < GR; ++g) {
             if ((uint32_t)g >= ng) break;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const uint32_t j = (jw[2 * g + e / 2] >> (16 * (e & 1))) & 0xffffu;
-                if (j != 0xffffu) {
-                    const uint32_t pos = atomicAdd(s_cnt + j, 1u);
+                const uint32_t r = (rk[2 * g + e / 2] >> (16 * (e & 1))) & 0xffffu;
+                if (r != 0xffffu) {
+                    const uint32_t h = key[4 * g + e];
+                    const uint32_t j = POW2 ? h & (BPB - 1) : min((uint32_t)(bucket_of_hash(h, H) - b0), nb - 1);
+                    const uint32_t pos = s_cnt[j] + r;
                     bad |= pos - a >= nk;
-                    if (pos < SB_BUF_KEYS) buf[pos] = key[4 * g + e];
+                    if (pos < SB_BUF_KEYS) buf[pos] = h;
                 }
             }
         }
@@ -1572,12 +1589,13 @@ constexpr uint32_t MAX_HUGE_SB = 1536;  // bins of more than SB_CAP keys with a 
 template <bool POW2>
 __global__ void __launch_bounds__(SB_THREADS, 1)
 k_big_count(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__ item_meta,
-            const Plan* __restrict__ plan, uint32_t* __restrict__ huge_count, uint32_t* err) {
+            const Plan* __restrict__ plan, uint32_t* __restrict__ huge_count, uint32_t* __restrict__ item_hot,
+            uint32_t* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
     uint32_t* const s_buf0 = s_cnt + BPB;  // buffer b at s_buf0 + b * SB_BUF_KEYS
     __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ uint32_t s_e[2], s_p[2], s_lo[2], s_hi[2];
+    __shared__ uint32_t s_e[2], s_p[2], s_lo[2], s_hi[2], s_wmax[SB_THREADS / 32];
     const uint32_t tid = threadIdx.x;
     const uint32_t items = plan->huge_chunks;
     const uint32_t G = gridDim.x;
@@ -1648,19 +1666,29 @@ k_big_count(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__
             }
         }
         __syncthreads();
-        // flush: thread t adds its 8 buckets' nonzero counts into the bin's, and clears them
+        // flush: thread t adds its 8 buckets' nonzero counts into the bin's, and
+        // clears them; the chunk's fullest bucket is recorded for k_big_place
         const uint32_t j0 = 8 * tid;
         {
             const uint4 c0 = *reinterpret_cast<const uint4*>(s_cnt + j0);
             const uint4 c1 = *reinterpret_cast<const uint4*>(s_cnt + j0 + 4);
             const uint32_t cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            uint32_t cmax = 0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < 8; ++u) {
                 if (cv[u]) atomicAdd(huge_count + (uint64_t)e * BPB + j0 + u, cv[u]);
+                cmax = max(cmax, (cv[u] << BIN_SHIFT) | (j0 + u));
+            }
             *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(0, 0, 0, 0);
             *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(0, 0, 0, 0);
+            cmax = __reduce_max_sync(FULL_MASK, cmax);
+            if (lane_id() == 0) s_wmax[tid >> 5] = cmax;
         }
         __syncthreads();
+        if (tid < 32) {
+            const uint32_t m = __reduce_max_sync(FULL_MASK, s_wmax[tid]);
+            if (tid == 0 && ok) item_hot[it] = m & (BPB - 1);
+        }
         if (tid == 0) start_copy(b, m2);
     }
     if (bad) atomicOr(err, DEVERR_BOUNDS);
@@ -1678,27 +1706,28 @@ k_big_count(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__
 template <bool POW2>
 __global__ void __launch_bounds__(SB_THREADS, 1)
 k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__ item_meta,
-            const Plan* __restrict__ plan, uint32_t* __restrict__ huge_cursor, uint64_t n,
-            uint32_t* __restrict__ out, uint32_t* err) {
+            const uint32_t* __restrict__ item_hot, const Plan* __restrict__ plan, uint32_t* __restrict__ huge_cursor,
+            uint64_t n, uint32_t* __restrict__ out, uint32_t* err) {
     constexpr int GR = SB_KPT / 4;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
     uint32_t* const s_buf0 = s_cnt + BPB;  // buffer b at s_buf0 + b * SB_BUF_KEYS
     __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ uint32_t s_e[2], s_p[2], s_lo[2], s_hi[2], s_wmax[SB_THREADS / 32], s_hot;
+    __shared__ uint32_t s_e[2], s_p[2], s_lo[2], s_hi[2], s_hot[2];
     const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
     const uint32_t items = plan->huge_chunks;
     const uint32_t G = gridDim.x;
     const uint32_t nn = (uint32_t)min(n, (uint64_t)0xffffffffu);
 
-    // thread 0: chunk (e, p, lo, hi) into buffer b (e = ~0u: none); its description
-    // is read one chunk ahead, so no phase waits on it
-    auto start_copy = [&](int b, uint4 m) {
+    // thread 0: chunk (e, p, lo, hi) with its fullest bucket jh into buffer b
+    // (e = ~0u: none); its description is read one chunk ahead, so no phase waits on it
+    auto start_copy = [&](int b, uint4 m, uint32_t jh) {
         const uint32_t e = m.x, p = m.y, lo = m.z, hi = m.w;
         s_e[b] = e;
         s_p[b] = p;
         s_lo[b] = lo;
         s_hi[b] = hi;
+        s_hot[b] = jh;
         if (e == ~0u || hi - lo > SB_CAP) return;  // none left / inconsistent plan (flagged by the CTA)
         const uint32_t klo = lo & ~3u, khi = (hi + 3) & ~3u;
         fence_proxy_async_smem();
@@ -1710,8 +1739,9 @@ k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__
         mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         const uint4 none = make_uint4(~0u, 0, 0, 0);
-        start_copy(0, blockIdx.x < items ? item_meta[blockIdx.x] : none);
-        start_copy(1, blockIdx.x + G < items ? item_meta[blockIdx.x + G] : none);
+        const uint32_t i1 = blockIdx.x + G;
+        start_copy(0, blockIdx.x < items ? item_meta[blockIdx.x] : none, blockIdx.x < items ? item_hot[blockIdx.x] : 0u);
+        start_copy(1, i1 < items ? item_meta[i1] : none, i1 < items ? item_hot[i1] : 0u);
     }
     *reinterpret_cast<uint4*>(s_cnt + 8 * tid) = make_uint4(0, 0, 0, 0);
     *reinterpret_cast<uint4*>(s_cnt + 8 * tid + 4) = make_uint4(0, 0, 0, 0);
@@ -1720,9 +1750,13 @@ k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__
     bool failed = false, bad = false;
     int b = 0;
     for (uint32_t it = blockIdx.x; it < items; it += G, b ^= 1) {
-        const uint32_t e = s_e[b], p = s_p[b], s0 = s_lo[b], s1 = s_hi[b];
+        const uint32_t e = s_e[b], p = s_p[b], s0 = s_lo[b], s1 = s_hi[b], jh = s_hot[b] & (BPB - 1);
         uint4 m2 = make_uint4(~0u, 0, 0, 0);  // (thread 0) the chunk after next
-        if (tid == 0 && it + 2 * G < items) m2 = item_meta[it + 2 * G];
+        uint32_t jh2 = 0;
+        if (tid == 0 && it + 2 * G < items) {
+            m2 = item_meta[it + 2 * G];
+            jh2 = item_hot[it + 2 * G];
+        }
         const bool ok = e != ~0u && s1 - s0 <= SB_CAP;
         bad |= !ok;
         if (ok) {
@@ -1742,18 +1776,25 @@ k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__
         const uint32_t b0 = p << BIN_SHIFT;
         const uint32_t nb = POW2 ? BPB : (uint32_t)min((uint64_t)BPB, H.B - b0);
         const uint32_t ng = nv > tid ? (nv - tid + SB_THREADS - 1) / SB_THREADS : 0u;
-        uint32_t key[SB_KPT], jw[2 * GR];
-        // histogram of the chunk's buckets (the words are the keys' hashes)
+        uint32_t key[SB_KPT], rk[2 * GR];
+        // histogram of the chunk's buckets (the words are the keys' hashes); each
+        // key's rank in its bucket is what its increment returns (16 bits per key,
+        // 0xffff = not a key of the chunk).  These bins hold the most duplicated
+        // keys: the lanes of a warp whose keys fall in the chunk's fullest bucket
+        // jh (counted by k_big_count) share one increment.
 #pragma unroll
         for (int g = 0; g < GR; ++g) {
             if ((uint32_t)g >= ng) break;
             const uint32_t v = tid + (uint32_t)g * SB_THREADS;
+            // the lanes of this warp that hold group g: those with tid + g * SB_THREADS < nv
+            const uint32_t first_v = g * SB_THREADS + w * 32;
+            const unsigned act = nv - first_v >= 32 ? FULL_MASK : (1u << (nv - first_v)) - 1u;
             const uint4 x = reinterpret_cast<const uint4*>(buf)[v];
             key[4 * g] = x.x;
             key[4 * g + 1] = x.y;
             key[4 * g + 2] = x.z;
             key[4 * g + 3] = x.w;
-            uint32_t js[4];
+            uint32_t rs[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const bool in_bin = 4 * v + u - a < nk;
@@ -1767,11 +1808,21 @@ k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__
                     bad |= in_bin && j >= nb;
                     j = min(j, nb - 1);
                 }
-                if (in_bin) atomicAdd(s_cnt + j, 1u);
-                js[u] = in_bin ? j : 0xffffu;
+                const bool hot = in_bin && j == jh;
+                const unsigned hm = __ballot_sync(act, hot);
+                uint32_t r = 0xffffu;
+                if (hot) {
+                    const int leader = __ffs(hm) - 1;
+                    uint32_t base = 0;
+                    if ((int)lane == leader) base = atomicAdd(s_cnt + jh, (uint32_t)__popc(hm));
+                    r = __shfl_sync(hm, base, leader) + __popc(hm & lanemask_lt());
+                } else if (in_bin) {
+                    r = atomicAdd(s_cnt + j, 1u);
+                }
+                rs[u] = r;
             }
-            jw[2 * g] = js[0] | (js[1] << 16);
-            jw[2 * g + 1] = js[2] | (js[3] << 16);
+            rk[2 * g] = rs[0] | (rs[1] << 16);
+            rk[2 * g + 1] = rs[2] | (rs[3] << 16);
         }
         __syncthreads();
         // reserve the chunk's run in every bucket it touches; thread t owns buckets [8t, 8t + 8)
@@ -1780,46 +1831,28 @@ k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__
             const uint4 c0 = *reinterpret_cast<const uint4*>(s_cnt + j0);
             const uint4 c1 = *reinterpret_cast<const uint4*>(s_cnt + j0 + 4);
             const uint32_t cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-            uint32_t base[8], cmax = 0;
+            uint32_t base[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 8; ++u)
                 base[u] = cv[u] ? atomicAdd(huge_cursor + (uint64_t)e * BPB + j0 + u, cv[u]) : 0u;
-                cmax = max(cmax, (cv[u] << BIN_SHIFT) | (j0 + u));
-            }
             *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(base[0], base[1], base[2], base[3]);
             *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(base[4], base[5], base[6], base[7]);
-            cmax = __reduce_max_sync(FULL_MASK, cmax);
-            if (lane == 0) s_wmax[w] = cmax;
         }
         __syncthreads();
-        if (w == 0) {
-            const uint32_t m = __reduce_max_sync(FULL_MASK, s_wmax[lane]);
-            if (lane == 0) s_hot = m & (BPB - 1);
-        }
-        __syncthreads();
-        // place every key (keys again from their hashes); the fullest bucket's keys a warp at a time
-        const uint32_t jh = s_hot;
+        // place every key at its bucket's run plus its rank (keys again from their
+        // hashes; the bucket again from the word); a warp's keys of the fullest
+        // bucket have consecutive ranks, so they go out as consecutive words
 #pragma unroll
         for (int g = 0; g < GR; ++g) {
             if ((uint32_t)g >= ng) break;
-            // the lanes of this warp that hold group g: those with tid + g * SB_THREADS < nv
-            const uint32_t first_v = g * SB_THREADS + w * 32;
-            const unsigned act = nv - first_v >= 32 ? FULL_MASK : (1u << (nv - first_v)) - 1u;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const uint32_t j = (jw[2 * g + u / 2] >> (16 * (u & 1))) & 0xffffu;
-                const unsigned hm = __ballot_sync(act, j == jh);
-                uint32_t pos = 0;
-                if (j == jh) {
-                    const int leader = __ffs(hm) - 1;
-                    uint32_t base = 0;
-                    if ((int)lane == leader) base = atomicAdd(s_cnt + jh, (uint32_t)__popc(hm));
-                    pos = __shfl_sync(hm, base, leader) + __popc(hm & lanemask_lt());
-                } else if (j != 0xffffu) {
-                    pos = atomicAdd(s_cnt + j, 1u);
-                }
-                if (j != 0xffffu) {
-                    if (pos < nn) out[pos] = unhash_key32(key[4 * g + u], H);
+                const uint32_t r = (rk[2 * g + u / 2] >> (16 * (u & 1))) & 0xffffu;
+                if (r != 0xffffu) {
+                    const uint32_t h = key[4 * g + u];
+                    const uint32_t j = POW2 ? h & (BPB - 1) : min((uint32_t)(bucket_of_hash(h, H) - b0), nb - 1);
+                    const uint32_t pos = s_cnt[j] + r;
+                    if (pos < nn) out[pos] = unhash_key32(h, H);
                     else bad = true;
                 }
             }
@@ -1828,7 +1861,7 @@ k_big_place(const uint32_t* __restrict__ in, Hasher H, const uint4* __restrict__
         *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(0, 0, 0, 0);
         *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(0, 0, 0, 0);
         __syncthreads();
-        if (tid == 0) start_copy(b, m2);  // the chunk after next, into this buffer
+        if (tid == 0) start_copy(b, m2, jh2);  // the chunk after next, into this buffer
     }
     if (bad) atomicOr(err, DEVERR_BOUNDS);
     if (failed && tid == 0) {
@@ -1939,6 +1972,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     const size_t o_plan = off; off += al(sizeof(Plan));
     const size_t o_hcur = off; off += al((size_t)max_huge * BPB * 4);
     const size_t o_items = off; off += al(max_items * sizeof(uint4));
+    const size_t o_ihot = off; off += al(max_items * 4);
     const size_t o_ka = off; off += al(two ? n * sizeof(K) : 0);
     const size_t o_va = off; off += al(two && hv ? n * 4 : 0);
     const size_t o_kb = off; off += al(n * sizeof(K));
@@ -1961,6 +1995,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     Plan* plan = reinterpret_cast<Plan*>(base + o_plan);
     uint32_t* huge_cursor = reinterpret_cast<uint32_t*>(base + o_hcur);
     uint4* item_meta = reinterpret_cast<uint4*>(base + o_items);
+    uint32_t* item_hot = reinterpret_cast<uint32_t*>(base + o_ihot);  // each chunk's fullest bucket
     K* ka = reinterpret_cast<K*>(base + o_ka);
     uint32_t* va = reinterpret_cast<uint32_t*>(base + o_va);
     K* kb = reinterpret_cast<K*>(base + o_kb);
@@ -2051,7 +2086,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
             if (r != cudaSuccess) return r;
             launch_begin("huge_count", s);
             kern<<<grid_for(kern, SB_THREADS, SB_SMEM), SB_THREADS, SB_SMEM, s>>>(
-                reinterpret_cast<const uint32_t*>(kb), t.H, item_meta, plan, huge_count, t.err);
+                reinterpret_cast<const uint32_t*>(kb), t.H, item_meta, plan, huge_count, item_hot, t.err);
             launch_end("huge_count", s);
             return cudaGetLastError();
         };
@@ -2114,7 +2149,7 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
             if (r != cudaSuccess) return r;
             launch_begin("bin_big", s);
             kern<<<grid_for(kern, SB_THREADS, SB_SMEM), SB_THREADS, SB_SMEM, s>>>(
-                reinterpret_cast<const uint32_t*>(kb), t.H, item_meta, plan, huge_cursor, n,
+                reinterpret_cast<const uint32_t*>(kb), t.H, item_meta, item_hot, plan, huge_cursor, n,
                 static_cast<uint32_t*>(t.keys), t.err);
             launch_end("bin_big", s);
             return cudaGetLastError();
