@@ -1361,6 +1361,11 @@ constexpr uint32_t SB_WAIT_LIMIT = 1u << 24;        // polls of a copy's barrier
 constexpr size_t SB_SMEM = (size_t)BPB * 4 + 2 * (size_t)SB_BUF_KEYS * 4;
 static_assert(BPB == 8 * SB_THREADS, "each thread scans eight buckets");
 
+// k_bin_small keeps a counter array per buffer, so that a bin's counters can
+// be cleared while the next bin is being counted
+constexpr size_t SB_SMEM_SMALL = 2 * (size_t)BPB * 4 + 2 * (size_t)SB_BUF_KEYS * 4;
+static_assert(SB_SMEM_SMALL + 1024 <= 227 * 1024, "k_bin_small's shared memory exceeds a CTA's");
+
 template <bool POW2, bool LONGS>
 __global__ void __launch_bounds__(SB_THREADS, 1)
 k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restrict__ bin_start,
@@ -1368,8 +1373,8 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
             uint32_t* __restrict__ out, uint32_t* err, LongFinder LF) {
     constexpr int GR = SB_KPT / 4;  // 16-byte groups of keys per thread
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* const s_buf0 = s_cnt + BPB;  // buffer b at s_buf0 + b * SB_BUF_KEYS
+    uint32_t* const s_cnt0 = reinterpret_cast<uint32_t*>(smem);  // buffer b's counters at s_cnt0 + b * BPB
+    uint32_t* const s_buf0 = s_cnt0 + 2 * BPB;                    // buffer b at s_buf0 + b * SB_BUF_KEYS
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_bin[2], s_lo[2], s_hi[2], s_wsum[SB_THREADS / 32];
     const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
@@ -1377,9 +1382,11 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
     const uint32_t G = gridDim.x;
 
     // Static schedule: this CTA takes small bins blockIdx.x, blockIdx.x + G, ...
-    // (they are of similar size).  Thread 0 starts the copy of bin (p, s0, s1)
-    // into buffer b; the bin's number and range are read one bin ahead, so no
-    // phase waits on them.
+    // (they are of similar size); bin i goes to buffer i % 2.  Thread 0 starts
+    // the copy of bin (p, s0, s1) into buffer b.  The first two bins are copied
+    // before the loop; bin i + 1 is copied into the buffer bin i - 1 used as soon
+    // as every thread has passed bin i's first barrier (so none still reads it).
+    // The bin's number and range are read one bin ahead, so no phase waits on them.
     auto start_copy = [&](int b, uint32_t p, uint32_t s0, uint32_t s1) {
         s_bin[b] = p;
         s_lo[b] = s0;
@@ -1400,8 +1407,8 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
             start_copy(b, p, p != ~0u ? __ldg(bin_start + p) : 0u, p != ~0u ? __ldg(bin_start + p + 1) : 0u);
         }
     }
-    *reinterpret_cast<uint4*>(s_cnt + 8 * tid) = make_uint4(0, 0, 0, 0);
-    *reinterpret_cast<uint4*>(s_cnt + 8 * tid + 4) = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(s_cnt0 + 16 * tid + 4 * c) = make_uint4(0, 0, 0, 0);
     __syncthreads();
     uint32_t parity = 0;  // bit b: the phase buffer b's barrier completes next
     bool failed = false, bad = false;
@@ -1409,22 +1416,19 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
     for (uint32_t it = blockIdx.x; it < n_small; it += G, b ^= 1) {
         const uint32_t p = s_bin[b];
         const uint32_t s0 = s_lo[b], s1 = s_hi[b];
-        // (thread 0) the bin two ahead: its number now, its range after the histogram
-        const uint32_t it2 = it + 2 * G;
-        uint32_t p2 = ~0u, lo2 = 0, hi2 = 0;
-        if (tid == 0 && it2 < n_small) p2 = __ldg(work + n_big + it2);
+        uint32_t* const s_cnt = s_cnt0 + b * BPB;
+        // (thread 0) the next bin but one: its number now, its range after the histogram
+        const uint32_t it1 = it + G;
+        uint32_t p1 = ~0u, lo1 = 0, hi1 = 0;
+        if (tid == 0 && it > blockIdx.x && it1 < n_small) p1 = __ldg(work + n_big + it1);
         const bool ok = s1 - s0 <= SB_CAP;
         bad |= !ok;  // (inconsistent plan: nothing was copied)
         if (ok) {
             uint32_t polls = 0;
             while (!mbar_test_parity(&s_bar[b], (parity >> b) & 1u) && ++polls < SB_WAIT_LIMIT) {
             }
-            failed = polls >= SB_WAIT_LIMIT;
+            failed |= polls >= SB_WAIT_LIMIT;
             parity ^= 1u << b;
-        }
-        if (__syncthreads_or(failed)) {
-            failed = true;
-            break;
         }
         const uint32_t nk = ok ? s1 - s0 : 0u;
         const uint32_t klo = s0 & ~3u;
@@ -1438,7 +1442,9 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
         // increment returns, kept in registers for the placement, two per word
         // (16 bits each: ranks are below SB_CAP; 0xffff = not a key of the bin).
         // (groups past the thread's last are skipped by a branch, which is the
-        // same for all lanes of a warp but the last one: no predicated-off work)
+        // same for all lanes of a warp but the last one: no predicated-off work.
+        // A copy that timed out leaves the buffer's old words, read here in
+        // bounds; the CTA then leaves at the barrier below.)
         const uint32_t ng = nv > tid ? (nv - tid + SB_THREADS - 1) / SB_THREADS : 0u;
         uint32_t key[SB_KPT], rk[2 * GR];
 #pragma unroll
@@ -1472,11 +1478,16 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
                 rk[2 * g + 1] = js[2] | (js[3] << 16);
             }
         }
-        if (tid == 0 && p2 != ~0u) {
-            lo2 = __ldg(bin_start + p2);
-            hi2 = __ldg(bin_start + p2 + 1);
+        if (tid == 0 && p1 != ~0u) {
+            lo1 = __ldg(bin_start + p1);
+            hi1 = __ldg(bin_start + p1 + 1);
         }
-        __syncthreads();
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        // every thread is past the previous bin: its buffer takes the next bin
+        if (tid == 0 && it > blockIdx.x) start_copy(b ^ 1, p1, lo1, hi1);
         // exclusive scan of the bin's counts: thread t owns buckets [8t, 8t + 8)
         const uint32_t j0 = 8 * tid;
         const uint4 c0 = *reinterpret_cast<const uint4*>(s_cnt + j0);
@@ -1488,13 +1499,11 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
         const uint32_t winc = warp_inclusive_scan(tsum);
         if (lane == 31) s_wsum[w] = winc;
         __syncthreads();
-        if (w == 0) {
-            const uint32_t x = s_wsum[lane];
-            s_wsum[lane] = warp_inclusive_scan(x) - x;
-        }
-        __syncthreads();
+        // every warp takes its prefix from the 32 warp sums itself (no second barrier)
+        const uint32_t xw = s_wsum[lane];
+        const uint32_t wpre = __shfl_sync(FULL_MASK, warp_inclusive_scan(xw) - xw, w);
         uint32_t st[8];
-        st[0] = s_wsum[w] + winc - tsum;
+        st[0] = wpre + winc - tsum;
 #pragma unroll
         for (int e = 1; e < 8; ++e) st[e] = st[e - 1] + cv[e - 1];
         if (ok) {
@@ -1537,7 +1546,9 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
         }
         __syncthreads();
         // the sorted bin out as keys (the words are hashes: fmix32_inv undoes them):
-        // 16-byte stores for the aligned body, single keys at the edges
+        // 16-byte stores for the aligned body, single keys at the edges.  The
+        // counters are cleared for the bin after next; no barrier ends the bin:
+        // the next bin's first barrier orders this buffer's reuse
         if (ok) {
             const uint32_t v0 = (s0 + 3) & ~3u, v1 = s1 & ~3u;  // aligned body [v0, v1) (empty if v1 <= v0)
             if (v1 > v0) {
@@ -1557,8 +1568,6 @@ k_bin_small(const uint32_t* __restrict__ in, Hasher H, const uint32_t* __restric
         }
         *reinterpret_cast<uint4*>(s_cnt + j0) = make_uint4(0, 0, 0, 0);
         *reinterpret_cast<uint4*>(s_cnt + j0 + 4) = make_uint4(0, 0, 0, 0);
-        __syncthreads();
-        if (tid == 0) start_copy(b, p2, lo2, hi2);  // the bin after next, into this buffer
     }
     if (bad) atomicOr(err, DEVERR_BOUNDS);
     if (failed && tid == 0) {
@@ -2129,10 +2138,10 @@ cudaError_t build_partitioned_impl(Table& t, const K* keys, const uint32_t* vals
     }
     if (e == cudaSuccess && small_path) {
         auto run = [&](auto kern) {
-            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB_SMEM);
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB_SMEM_SMALL);
             if (r != cudaSuccess) return r;
             launch_begin("bin_small", s);
-            kern<<<grid_for(kern, SB_THREADS, SB_SMEM), SB_THREADS, SB_SMEM, s>>>(
+            kern<<<grid_for(kern, SB_THREADS, SB_SMEM_SMALL), SB_THREADS, SB_SMEM_SMALL, s>>>(
                 reinterpret_cast<const uint32_t*>(kb), t.H, bin_start, work, plan, t.offsets,
                 static_cast<uint32_t*>(t.keys), t.err, t.finder);
             launch_end("bin_small", s);

@@ -1117,8 +1117,9 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
             const uint32_t prev = __shfl_up_sync(FULL_MASK, k, 1);
             const bool head = lane < nv && (lane == 0 || k != prev);
             const unsigned hm = __ballot_sync(FULL_MASK, head);
-            const unsigned above = lane == 31 ? 0u : (hm & ~((2u << lane) - 1u));
-            len = (above ? (uint32_t)(__ffs(above) - 1) : nv) - lane;
+            // the next head above this lane (none: __ffs gives 0, and the run ends at nv)
+            const unsigned above = hm & (0xfffffffeu << lane);
+            len = min((uint32_t)__ffs(above) - 1u, nv) - lane;
             return head;
         };
         const uint32_t nseg = s_nseg;
