@@ -267,88 +267,101 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T* total) {
 // coarse segment in the second pass); offsets[B] = n; the huge bins (more
 // than huge_t keys; the first max_huge of them) with the prefix of their
 // chunk counts; and the work list of the other bins, bins above big_t keys first.
-__global__ void __launch_bounds__(1024)
+// Thread t holds the counts of bins [16t, 16t + 16) in registers, so every
+// list comes from one block-wide scan of per-thread totals.
+constexpr int PLAN_THREADS = 1024;
+constexpr int PLAN_PB = MAX_BINS / PLAN_THREADS;  // bins per thread
+__global__ void __launch_bounds__(PLAN_THREADS)
 k_part_plan(const uint32_t* __restrict__ bin_count, uint32_t P, uint32_t P1, uint32_t P2, uint64_t n,
-            uint32_t big_t, uint32_t huge_t, uint32_t huge_chunk, uint32_t max_huge, uint32_t* bin_start, uint32_t* seg_chunk_start, uint32_t* work, uint32_t* huge_bin,
-            uint32_t* huge_chunk_start, Plan* plan, uint32_t* offsets, uint64_t B) {
+            uint32_t big_t, uint32_t huge_t, uint32_t huge_chunk, uint32_t max_huge, uint32_t* bin_start,
+            uint32_t* seg_chunk_start, uint32_t* work, uint32_t* huge_bin, uint32_t* huge_chunk_start, Plan* plan,
+            uint32_t* offsets, uint64_t B) {
     __shared__ uint32_t s_warp[33];
-    __shared__ uint32_t s_huge[MAX_BINS / 32];
-    uint32_t running = 0, tot;
-    for (uint32_t i = threadIdx.x; i < MAX_BINS / 32; i += blockDim.x) s_huge[i] = 0;
-    for (uint32_t base = 0; base < P; base += blockDim.x) {
-        const uint32_t p = base + threadIdx.x;
-        const uint32_t c = p < P ? bin_count[p] : 0u;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(c, s_warp, &tot);
-        if (p < P) bin_start[p] = running + ex;
-        running += tot;
+    const uint32_t tid = threadIdx.x, p0 = tid * PLAN_PB;
+    uint32_t c[PLAN_PB];
+    uint32_t sum = 0, nh_loc = 0;
+#pragma unroll
+    for (int i = 0; i < PLAN_PB; ++i) {
+        c[i] = p0 + i < P ? __ldg(bin_count + p0 + i) : 0u;
+        sum += c[i];
+        nh_loc += (p0 + i < P && c[i] > huge_t) ? 1u : 0u;
     }
-    if (threadIdx.x == 0) {
-        bin_start[P] = running;
+    // bin starts
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan<uint32_t>(sum, s_warp, &tot);
+#pragma unroll
+    for (int i = 0; i < PLAN_PB; ++i) {
+        if (p0 + i < P) bin_start[p0 + i] = run;
+        run += c[i];
+    }
+    if (tid == 0) {
+        bin_start[P] = tot;
         if (offsets) offsets[B] = (uint32_t)n;
     }
-    __syncthreads();
-    // second-pass chunks per coarse segment
-    uint32_t crun = 0;
-    for (uint32_t base = 0; base < P1; base += blockDim.x) {
-        const uint32_t sg = base + threadIdx.x;
-        uint32_t t = 0;
-        if (sg < P1) {
-            const uint32_t lo = bin_start[sg * P2];
-            const uint32_t hi = bin_start[min((sg + 1) * P2, P)];
-            t = (hi - lo + CHUNK - 1) / CHUNK;
+    // huge bins in index order (the first max_huge are admitted), their chunks,
+    // and the other bins by size
+    uint32_t nh_tot;
+    const uint32_t hx0 = block_exclusive_scan<uint32_t>(nh_loc, s_warp, &nh_tot);
+    uint32_t ch_loc = 0, nb_loc = 0, ns_loc = 0;
+    {
+        uint32_t hx = hx0;
+#pragma unroll
+        for (int i = 0; i < PLAN_PB; ++i) {
+            const bool in = p0 + i < P;
+            const bool huge = in && c[i] > huge_t;
+            const bool adm = huge && hx < max_huge;
+            hx += huge ? 1u : 0u;
+            if (adm) ch_loc += (c[i] + huge_chunk - 1) / huge_chunk;
+            if (in && !adm) {
+                if (c[i] > big_t) ++nb_loc;
+                else ++ns_loc;
+            }
         }
-        const uint32_t ex = block_exclusive_scan<uint32_t>(t, s_warp, &tot);
-        if (sg < P1) seg_chunk_start[sg] = crun + ex;
-        crun += tot;
     }
-    // huge bins (index order, first max_huge) and their chunk prefix
-    uint32_t nh = 0, cr = 0;
-    for (uint32_t base = 0; base < P; base += blockDim.x) {
-        const uint32_t p = base + threadIdx.x;
-        const uint32_t c = p < P ? bin_count[p] : 0u;
-        const uint32_t is_huge = c > huge_t ? 1u : 0u;
-        const uint32_t hx = block_exclusive_scan<uint32_t>(is_huge, s_warp, &tot);
-        const bool admit = is_huge && nh + hx < max_huge;
-        const uint32_t ch = admit ? (c + huge_chunk - 1) / huge_chunk : 0u;
-        uint32_t ctot;
-        const uint32_t cx = block_exclusive_scan<uint32_t>(ch, s_warp, &ctot);
-        if (admit) {
-            huge_bin[nh + hx] = p;
-            huge_chunk_start[nh + hx] = cr + cx;
-            atomicOr(&s_huge[p >> 5], 1u << (p & 31));
+    uint32_t ch_tot, nb_tot, ns_tot;
+    uint32_t cx = block_exclusive_scan<uint32_t>(ch_loc, s_warp, &ch_tot);
+    uint32_t bx = block_exclusive_scan<uint32_t>(nb_loc, s_warp, &nb_tot);
+    uint32_t sx = block_exclusive_scan<uint32_t>(ns_loc, s_warp, &ns_tot);
+    {
+        uint32_t hx = hx0;
+#pragma unroll
+        for (int i = 0; i < PLAN_PB; ++i) {
+            const uint32_t p = p0 + i;
+            const bool in = p < P;
+            const bool huge = in && c[i] > huge_t;
+            const bool adm = huge && hx < max_huge;
+            if (adm) {
+                huge_bin[hx] = p;
+                huge_chunk_start[hx] = cx;
+                cx += (c[i] + huge_chunk - 1) / huge_chunk;
+            }
+            hx += huge ? 1u : 0u;
+            if (in && !adm) {
+                if (c[i] > big_t) work[bx++] = p;
+                else work[nb_tot + sx++] = p;
+            }
         }
-        nh += tot;
-        cr += ctot;
     }
-    const uint32_t n_huge = min(nh, max_huge);
-    __syncthreads();
-    // work list: big bins first, then the rest
-    uint32_t nbig = 0;
-    for (uint32_t base = 0; base < P; base += blockDim.x) {
-        const uint32_t p = base + threadIdx.x;
-        const bool hz = p < P && ((s_huge[p >> 5] >> (p & 31)) & 1u);
-        const uint32_t big = (p < P && !hz && bin_count[p] > big_t) ? 1u : 0u;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(big, s_warp, &tot);
-        if (big) work[nbig + ex] = p;
-        nbig += tot;
+    const uint32_t n_huge = min(nh_tot, max_huge);
+    __syncthreads();  // bin_start is complete
+    // second-pass chunks per coarse segment (P1 <= RADIX segments)
+    uint32_t t = 0;
+    if (tid < P1) {
+        const uint32_t lo = bin_start[tid * P2];
+        const uint32_t hi = bin_start[min((tid + 1) * P2, P)];
+        t = (hi - lo + CHUNK - 1) / CHUNK;
     }
-    uint32_t nsmall = 0;
-    for (uint32_t base = 0; base < P; base += blockDim.x) {
-        const uint32_t p = base + threadIdx.x;
-        const bool hz = p < P && ((s_huge[p >> 5] >> (p & 31)) & 1u);
-        const uint32_t small = (p < P && !hz && bin_count[p] <= big_t) ? 1u : 0u;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(small, s_warp, &tot);
-        if (small) work[nbig + nsmall + ex] = p;
-        nsmall += tot;
-    }
-    if (threadIdx.x == 0) {
+    uint32_t crun;
+    const uint32_t sc = block_exclusive_scan<uint32_t>(t, s_warp, &crun);
+    if (tid < P1) seg_chunk_start[tid] = sc;
+    if (tid == 0) {
         seg_chunk_start[P1] = crun;
-        huge_chunk_start[n_huge] = cr;
+        huge_chunk_start[n_huge] = ch_tot;
         plan->chunks_b = crun;
         plan->n_huge = n_huge;
-        plan->huge_chunks = cr;
-        plan->n_work = nbig + nsmall;
-        plan->n_big = nbig;
+        plan->huge_chunks = ch_tot;
+        plan->n_work = nb_tot + ns_tot;
+        plan->n_big = nb_tot;
         plan->huge_chunk = huge_chunk;
     }
 }
@@ -362,8 +375,11 @@ __global__ void __launch_bounds__(1024)
 k_chunk_scan(uint32_t* cnt, uint32_t* pref, ChunkMap cm, uint32_t nch_host, const Plan* __restrict__ plan, uint32_t R,
              uint32_t dig_mul, const uint32_t* __restrict__ digit_total) {
     __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_scs[RADIX + 1];  // segmented: the segments' first chunks
     const uint32_t nch = cm.segmented ? plan->chunks_b : nch_host;
     const uint32_t d = blockIdx.x;
+    if (cm.segmented)
+        for (uint32_t i = threadIdx.x; i <= cm.nseg && i <= RADIX; i += blockDim.x) s_scs[i] = cm.seg_chunk_start[i];
     const uint32_t per = (nch + blockDim.x - 1) / blockDim.x;
     const uint32_t c0 = min(nch, threadIdx.x * per), c1 = min(nch, c0 + per);
     uint32_t sum = 0;
@@ -376,20 +392,34 @@ k_chunk_scan(uint32_t* cnt, uint32_t* pref, ChunkMap cm, uint32_t nch_host, cons
     }
     __syncthreads();
     // subtract the prefix at the segment's first chunk, add the digit's start
+    // (a thread's chunks are consecutive: the segment is looked up in shared
+    // memory, and the start read again only when the segment changes)
+    uint32_t seg = ~0u, first = 0, start = 0, pfirst = 0;
     for (uint32_t c = c0; c < c1; ++c) {
-        uint32_t seg, first;
-        uint64_t lo, hi;
-        chunk_range(cm, c, seg, first, lo, hi);
-        uint32_t start = 0;
-        if (d < R) {
-            if (digit_total) {
-                for (uint32_t q = 0; q < d; ++q) start += digit_total[q];
-            } else {
-                const uint32_t bin = cm.segmented ? seg * cm.P2 + d : d * dig_mul;
-                start = cm.bin_start[min(bin, cm.P)];
+        uint32_t sg = 0;
+        if (cm.segmented) {  // last segment with s_scs[s] <= c
+            uint32_t lo = 0, hi = min(cm.nseg, RADIX);
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_scs[mid] <= c) lo = mid; else hi = mid;
             }
+            sg = lo;
         }
-        cnt[(uint64_t)c * RADIX + d] = start + pref[(uint64_t)c * RADIX + d] - pref[(uint64_t)first * RADIX + d];
+        if (sg != seg) {
+            seg = sg;
+            first = cm.segmented ? s_scs[sg] : 0u;
+            start = 0;
+            if (d < R) {
+                if (digit_total) {
+                    for (uint32_t q = 0; q < d; ++q) start += digit_total[q];
+                } else {
+                    const uint32_t bin = cm.segmented ? seg * cm.P2 + d : d * dig_mul;
+                    start = cm.bin_start[min(bin, cm.P)];
+                }
+            }
+            pfirst = pref[(uint64_t)first * RADIX + d];
+        }
+        cnt[(uint64_t)c * RADIX + d] = start + pref[(uint64_t)c * RADIX + d] - pfirst;
     }
 }
 
