@@ -865,7 +865,11 @@ k_probe_bins(const K* __restrict__ qs, const uint32_t* __restrict__ qbin_start, 
 // not tried).
 constexpr uint32_t HJ_SLOTS = 4096;                   // table words (32 KiB)
 constexpr uint32_t HJ_MAX_FILL = HJ_SLOTS * 3 / 4;    // distinct keys before the bin falls back
-constexpr uint32_t HJ_KEY_BYTES = 80 * 1024;          // staged keys (two CTAs per SM)
+constexpr uint32_t HJ_OVF = 512;                      // bucket-indexed table: overflow words (4 KiB)
+constexpr uint32_t HJ_OVF_MAX = HJ_OVF * 3 / 4;       // overflow keys before the bin falls back
+constexpr uint32_t HJ_TABLE_BYTES = BIN_BUCKETS * 4 + HJ_OVF * 8;  // either table (36 KiB)
+constexpr uint32_t HJ_KEY_BYTES = 76 * 1024;          // staged keys (two CTAs per SM)
+static_assert(HJ_SLOTS * 8 <= HJ_TABLE_BYTES, "the hashed table fits the table region");
 constexpr int HJ_THREADS = 768;                       // two CTAs (48 warps) per SM: 512 took 1.29 ms, 768 1.14
 constexpr uint32_t HJ_TRY_LIMIT = 64;                 // fallbacks before the try-rate test applies
 constexpr int HJ_QUNROLL = 4;                         // query loads in flight per thread
@@ -883,17 +887,38 @@ __device__ __forceinline__ void hj_probe_seq(uint32_t h, uint32_t& slot, uint32_
     step = (x >> 7) | 1u;
 }
 static_assert(HJ_SLOTS == 4096, "hj_probe_seq returns 12-bit slots");
+// The same for the bucket-indexed table's overflow words.
+__device__ __forceinline__ void hj_ovf_seq(uint32_t h, uint32_t& slot, uint32_t& step) {
+    const uint32_t x = h * 0x9e3779b1u;
+    slot = x >> (32 - 9);
+    step = (x >> 7) | 1u;
+}
+static_assert(HJ_OVF == 512, "hj_ovf_seq returns 9-bit slots");
 
-template <int OUT, bool TOTAL>
+//
+// DM (B = 2^lb with lb >= 16, so a bucket's place in its bin is the low 13 bits
+// of the hash, and its keys differ only in the lb..31 bits): the table is
+// indexed by bucket instead, a 32-bit word per bucket of the bin holding
+// (overflow flag << 31 | tag << (lb - 1) | count), tag = h >> lb, so a query
+// is one shared-memory load and compare.  A bucket's second and later distinct
+// keys (and a hot bin's summary entries, whose counts need 32 bits) go to a
+// small double-hashed table of (count << 32 | h) words, which the bucket's flag
+// sends a query to.  A bin whose overflow exceeds HJ_OVF_MAX keys falls back.
+// Counts in a bucket's word stay below 2^(lb-1) >= 2^15: it counts staged keys.
+template <int OUT, bool TOTAL, bool DM>
 __global__ void __launch_bounds__(HJ_THREADS, 2)
 k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_start, BinWork W,
              const uint32_t* __restrict__ keys, const uint32_t* __restrict__ offs, uint64_t B, uint32_t n_keys,
              void* counts, uint64_t* total, uint32_t* work_ctr, uint32_t* fb_list, uint32_t* fb_n, uint32_t* tries,
-             uint32_t* err, LongSummary S, uint32_t hseed) {
+             uint32_t* err, LongSummary S, uint32_t hseed, uint32_t lb) {
+    static_assert(HJ_KEY_BYTES + HJ_TABLE_BYTES <= 112 * 1024, "two CTAs per SM");
     const bool qhashed = (W.qunhash >> 32) != 0;
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned long long* s_ht = reinterpret_cast<unsigned long long*>(smem);
-    unsigned char* const s_buf = smem + HJ_SLOTS * 8;
+    unsigned long long* s_ht = reinterpret_cast<unsigned long long*>(smem);   // !DM
+    uint32_t* const s_tab = reinterpret_cast<uint32_t*>(smem);                 // DM: a word per bucket
+    unsigned long long* const s_ovf = reinterpret_cast<unsigned long long*>(smem + BIN_BUCKETS * 4);
+    const uint32_t cbits = lb - 1, cmask = (1u << cbits) - 1u;
+    unsigned char* const s_buf = smem + HJ_TABLE_BYTES;
     const uint32_t* s_keys = reinterpret_cast<const uint32_t*>(s_buf);
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_p, s_bin, s_k0, s_k1, s_q0, s_q1, s_fill, s_abort, s_hot, s_skip;
@@ -972,7 +997,8 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
         s_fill = 0;
         s_abort = 0;
     }
-    for (uint32_t t = threadIdx.x; t < HJ_SLOTS; t += blockDim.x) s_ht[t] = 0ull;
+    for (uint32_t t = threadIdx.x; t < HJ_TABLE_BYTES / 16; t += blockDim.x)
+        reinterpret_cast<uint4*>(smem)[t] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     while (true) {
         // here: the table is empty, and the copy of item s_p's keys is in flight
@@ -1091,8 +1117,54 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
         // insert per run; two steps per iteration for independent loads
         // the table holds each key's hash h = fmix32(k ^ seed) (a bijection, so
         // equal hashes are equal keys), the form in which the grouped queries come
+        // DM: (count << 32 | h) into the overflow words
+        auto ovf_insert = [&](uint32_t h, uint32_t len) {
+            const unsigned long long add = (unsigned long long)len << 32;
+            uint32_t sl, stp;
+            hj_ovf_seq(h, sl, stp);
+            for (uint32_t t = 0; t < HJ_OVF; ++t) {
+                unsigned long long w = *static_cast<volatile unsigned long long*>(&s_ovf[sl]);
+                if (w == 0ull) {
+                    w = atomicCAS(&s_ovf[sl], 0ull, add | h);
+                    if (w == 0ull) {
+                        if (atomicAdd(&s_fill, 1u) + 1 > HJ_OVF_MAX) s_abort = 1;
+                        return;
+                    }
+                }
+                if ((uint32_t)w == h) {
+                    atomicAdd(&s_ovf[sl], add);
+                    return;
+                }
+                sl = (sl + stp) & (HJ_OVF - 1);
+            }
+            s_abort = 1;  // (full: the fill limit stops the bin first)
+        };
+        // DM: the key with hash h, len times; to_ovf: straight to the overflow words
+        auto dm_insert = [&](uint32_t h, uint32_t len, bool to_ovf) {
+            uint32_t* const slot = s_tab + (h & (BIN_BUCKETS - 1));
+            const uint32_t tag = h >> lb;
+            uint32_t w = *static_cast<volatile uint32_t*>(slot);
+            while (!to_ovf) {
+                if ((w & cmask) == 0u) {  // no key in this bucket yet (its flag may be set)
+                    const uint32_t old = atomicCAS(slot, w, w | (tag << cbits) | len);
+                    if (old == w) return;
+                    w = old;
+                } else if (((w & 0x7fffffffu) >> cbits) == tag) {
+                    atomicAdd(slot, len);
+                    return;
+                } else {
+                    break;  // another key holds the bucket's word
+                }
+            }
+            if (!(w >> 31)) atomicOr(slot, 0x80000000u);
+            ovf_insert(h, len);
+        };
         auto insert = [&](uint32_t key, uint32_t len) {
             const uint32_t k = fmix32(key ^ hseed);
+            if (DM) {
+                dm_insert(k, len, false);
+                return;
+            }
             const unsigned long long add = (unsigned long long)len << 32;
             uint32_t sl, stp;
             hj_probe_seq(k, sl, stp);
@@ -1143,7 +1215,11 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
             const uint32_t l = s_long_l[warp];
             const uint32_t n = __ldg(S.len + l);
             const uint32_t* sk = static_cast<const uint32_t*>(S.keys) + (size_t)l * SUM_SLOTS;
-            for (uint32_t e = lane; e < n; e += 32) insert(__ldg(sk + e), __ldg(S.cnt + (size_t)l * SUM_SLOTS + e));
+            for (uint32_t e = lane; e < n; e += 32) {
+                const uint32_t key = __ldg(sk + e), c = __ldg(S.cnt + (size_t)l * SUM_SLOTS + e);
+                if (DM) dm_insert(fmix32(key ^ hseed), c, true);
+                else insert(key, c);
+            }
         }
         __syncthreads();
         const bool abort = s_abort != 0;
@@ -1175,15 +1251,32 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
                         // the query's hash (grouped 32-bit queries already are hashes)
                         const uint32_t qk = qhashed ? kq[u] : fmix32(kq[u] ^ hseed);
                         uint32_t sl, stp, cnt = 0;
-                        hj_probe_seq(qk, sl, stp);
-                        for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
-                            const unsigned long long w = s_ht[sl];
-                            if (w == 0ull) break;
-                            if ((uint32_t)w == qk) {
-                                cnt = (uint32_t)(w >> 32);
-                                break;
+                        if (DM) {
+                            const uint32_t w = s_tab[qk & (BIN_BUCKETS - 1)];
+                            if (((w & 0x7fffffffu) >> cbits) == (qk >> lb)) cnt = w & cmask;
+                            if (cnt == 0u && (w >> 31)) {
+                                hj_ovf_seq(qk, sl, stp);
+                                for (uint32_t t = 0; t < HJ_OVF; ++t) {
+                                    const unsigned long long x = s_ovf[sl];
+                                    if (x == 0ull) break;
+                                    if ((uint32_t)x == qk) {
+                                        cnt = (uint32_t)(x >> 32);
+                                        break;
+                                    }
+                                    sl = (sl + stp) & (HJ_OVF - 1);
+                                }
                             }
-                            sl = (sl + stp) & (HJ_SLOTS - 1);
+                        } else {
+                            hj_probe_seq(qk, sl, stp);
+                            for (uint32_t t = 0; t < HJ_SLOTS; ++t) {
+                                const unsigned long long w = s_ht[sl];
+                                if (w == 0ull) break;
+                                if ((uint32_t)w == qk) {
+                                    cnt = (uint32_t)(w >> 32);
+                                    break;
+                                }
+                                sl = (sl + stp) & (HJ_SLOTS - 1);
+                            }
                         }
                         if (OUT == OUT_U32) static_cast<uint32_t*>(counts)[i] = cnt;
                         acc += cnt;
@@ -1194,7 +1287,8 @@ k_probe_hash(const uint32_t* __restrict__ qs, const uint32_t* __restrict__ qbin_
             }
         }
         __syncthreads();  // the table's last reader is done
-        for (uint32_t t = threadIdx.x; t < HJ_SLOTS; t += blockDim.x) s_ht[t] = 0ull;
+        for (uint32_t t = threadIdx.x; t < HJ_TABLE_BYTES / 16; t += blockDim.x)
+            reinterpret_cast<uint4*>(smem)[t] = make_uint4(0, 0, 0, 0);
         __syncthreads();
     }
     if (failed) {
@@ -1216,8 +1310,12 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
     // [2] fallback list length, [3..4] bins tried / given up by the hash join
     const uint32_t* list = nullptr;
     if constexpr (sizeof(K) == 4) {
-        auto kern = k_probe_hash<OUT, TOTAL>;
-        const size_t smem = (size_t)HJ_SLOTS * 8 + HJ_KEY_BYTES;
+        // the bucket-indexed table when B = 2^lb, lb >= 16
+        uint32_t lb = 0;
+        while (lb < 63 && (1ull << lb) < t.B) ++lb;
+        const bool dm = t.H.mode == MODE_POW2 && (1ull << lb) == t.B && lb >= 16 && lb <= 31;
+        auto kern = dm ? k_probe_hash<OUT, TOTAL, true> : k_probe_hash<OUT, TOTAL, false>;
+        const size_t smem = (size_t)HJ_TABLE_BYTES + HJ_KEY_BYTES;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
@@ -1226,7 +1324,7 @@ cudaError_t run_probe_bins(const Table& t, const GroupedQueries& g, void* counts
         launch_begin("probe_hash", s);
         kern<<<num_sms() * per_sm, HJ_THREADS, smem, s>>>(qs, g.bin_start, g.items, keys, t.offsets, t.B, (uint32_t)t.n,
                                                           counts, total, ctrs, fb_list, ctrs + 2, ctrs + 3, t.err, t.sum,
-                                                          (uint32_t)t.H.seed);
+                                                          (uint32_t)t.H.seed, dm ? lb : 16u);
         launch_end("probe_hash", s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

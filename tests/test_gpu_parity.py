@@ -293,13 +293,14 @@ def test_grouped_probe_zipf_u32_two_passes(hg):
     _probe_only(hg, wl.keys, 1 << 23, wl.queries)
 
 
-def test_grouped_hash_join_bins(hg):
+@pytest.mark.parametrize("B", [1 << 23, (1 << 23) - 9])
+def test_grouped_hash_join_bins(hg, B):
     # 1024 bins of ~8192 Zipf keys (at most a few hundred distinct each): the
     # grouped probe counts each bin through a shared-memory table of its
-    # distinct keys.  Bins 3, 7 and 500 get ~4000 extra distinct keys, more
-    # than the table takes, and fall back to the walking probe; the keys 0 and
-    # 2^32 - 1 (the table's empty marker) occur many times.
-    B = 1 << 23
+    # distinct keys (B = 2^23: a word per bucket; otherwise double hashing).
+    # Bins 3, 7 and 500 get ~4000 extra distinct keys, more than the table
+    # takes, and fall back to the walking probe; the keys 0 and 2^32 - 1 (the
+    # table's empty marker) occur many times.
     wl = W.zipf_large(n=(1 << 23) + 11, num_buckets=B, q=(1 << 21) + 3, M=1 << 18, salt=13)
     keys = wl.keys.copy()
     keys[::97] = 0xFFFFFFFF
@@ -312,6 +313,48 @@ def test_grouped_hash_join_bins(hg):
     queries[::50] = 0xFFFFFFFF
     queries[7::51] = 0
     queries[: extra.size] = extra
+    _probe_only(hg, keys, B, queries)
+
+
+def _fmix32_inv(h: np.ndarray) -> np.ndarray:
+    """Keys with the given MurmurHash3 fmix32 values (seed 0): the finaliser's
+    steps undone in reverse order (its multipliers' inverses mod 2^32)."""
+    h = h.astype(np.uint64)
+    m = np.uint64(0xFFFFFFFF)
+    h ^= h >> np.uint64(16)
+    h = (h * np.uint64(0x7ED1B41D)) & m
+    h ^= (h >> np.uint64(13)) ^ (h >> np.uint64(26))
+    h = (h * np.uint64(0xA5CB9243)) & m
+    h ^= h >> np.uint64(16)
+    return h.astype(np.uint32)
+
+
+def test_grouped_hash_join_shared_buckets(hg):
+    # B = 2^23: the hash join keeps a word per bucket, and a bucket's second and
+    # later distinct keys go to overflow words.  Keys built from chosen hashes
+    # put 2 to 4 distinct keys (1 to 5 copies each) into 60 buckets of each of
+    # bins 10..13, and queries hit each of them and miss with other tags in
+    # the same buckets.
+    B = 1 << 23
+    wl = W.zipf_large(n=(1 << 23) + 11, num_buckets=B, q=(1 << 21) + 3, M=1 << 18, salt=16)
+    rng = np.random.default_rng(17)
+    hashes, copies, misses = [], [], []
+    for p in range(10, 14):
+        for j in rng.choice(8192, size=60, replace=False):
+            tags = rng.choice(512, size=6, replace=False)
+            nd = int(rng.integers(2, 5))
+            for t in tags[:nd]:
+                hashes.append((int(t) << 23) | (p << 13) | int(j))
+                copies.append(int(rng.integers(1, 6)))
+            misses += [(int(t) << 23) | (p << 13) | int(j) for t in tags[nd:]]
+    built = _fmix32_inv(np.array(hashes, dtype=np.uint64))
+    assert np.array_equal(oracle.buckets(built, B, 0), np.array(hashes, dtype=np.uint64) & np.uint64(B - 1))
+    keys = np.concatenate([wl.keys, np.repeat(built, copies)])
+    keys = keys[rng.permutation(keys.size)]
+    queries = wl.queries.copy()
+    probe = np.concatenate([built, _fmix32_inv(np.array(misses, dtype=np.uint64))])
+    queries[: probe.size] = probe
+    queries[probe.size: 2 * probe.size] = probe
     _probe_only(hg, keys, B, queries)
 
 
