@@ -254,6 +254,25 @@ def test_two_pass_partition_with_hot_buckets(hg):
     _run_all(hg, wl.keys, B, 0, wl.queries, flags=hg.HG_INDEX_VALUES, check_gather=False)
 
 
+@pytest.mark.parametrize("case", ["u64_values", "u64", "u32_values"])
+def test_partition_bins_larger_than_the_stage(hg, case):
+    # 64 bins of ~16,400 nearly distinct keys: more than the bin sort's staging
+    # buffer holds for these widths, and no threshold on bucket size leaves few
+    # enough keys to stage, so every key is placed straight at its bucket's
+    # cursor; a few hot keys add buckets of 64 or more keys
+    B = (1 << 19) + 3
+    if case == "u32_values":
+        wl = W.plain_uniform((1 << 20) + 7, 1 << 14, num_buckets=B, salt=21)
+        keys, vals = wl.keys.copy(), np.arange(wl.keys.size, dtype=np.uint32)
+        keys[::4099] = keys[11]
+        keys[5::8191] = keys[13]
+    else:
+        wl = W.join_kv(n=(1 << 20) + 7, num_buckets=B, q=1 << 14, salt=22)
+        keys, vals = wl.keys.copy(), (wl.values if case == "u64_values" else None)
+        keys[::4099] = keys[11]
+    _run_all(hg, keys, B, 0, wl.queries, values=vals, check_gather=False, modes=("partition",))
+
+
 def test_partition_u64_values_many_bins(hg):
     B = 1 << 23
     wl = W.join_kv(n=1 << 22, num_buckets=B, q=1 << 15, salt=6)
