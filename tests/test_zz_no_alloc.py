@@ -8,8 +8,9 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
-from tests.hg_testutil import from_dev, table_arrays, to_dev
+from tests.hg_testutil import assert_same_table, from_dev, table_arrays, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +63,9 @@ def _same_as_hg_build(hg, keys, B, seed, values=None, flags=0, offs_shift=0, no_
     o = from_dev(offs, np.uint32)
     assert np.array_equal(o, o_ref)  # offsets bit-exact
     k = from_dev(kout, dt)
+    # and against the oracle: offsets bit-exact, every bucket's (key, value) multiset
+    ref = oracle.build_table(keys, B, seed, values=values, index_values=bool(flags & hg.HG_INDEX_VALUES))
+    assert_same_table(o, k, None if vout is None else from_dev(vout, np.uint32), ref)
     seg = np.repeat(np.arange(B, dtype=np.int64), np.diff(o.astype(np.int64)))
     if vout is None:
         assert np.array_equal(k[np.lexsort((k, seg))], k_ref[np.lexsort((k_ref, seg))])
